@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Throughput of grayscale morphological reconstruction on GB300.
+
+One step = the whole reconstruction of one batch of synthetic tiles through
+the C ABI (marker reset from its pristine copy, validation, scan pairs, queue
+propagation, neighbour notification, persistent launch replayed from a CUDA
+graph). Default workload "single4096": one 4096 x 4096 mask with 6711 blobs,
+reconstructed four times per step (4- and 8-connectivity x h-dome and
+fill-holes markers) as one 4-tile batch. Metric: reconstructed Mpix/s.
+
+Timing: CUDA events on the library's stream around each step; L2 is flushed
+(a 512 MiB write) before every timed step, outside the events. Under torchrun
+each rank runs the same batch (tiles are independent: weak scaling) and the
+slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+ALG_BYTES_PER_PX = 3  # read I, read J, write R: compulsory traffic of one reconstruction
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi while running."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def workload_tiles(name):
+    import synth
+    if name == "single4096":
+        w = synth.workload("single4096")
+        return w, w.tiles, True
+    w = synth.workload(name)
+    return w, w.tiles, False
+
+
+def gen_host(w, tiles, shared_mask):
+    """Pinned host tensors: masks and pristine markers for every tile."""
+    import numpy as np
+    import torch
+    import synth
+    if shared_mask:
+        pairs = synth.generate(tiles, w.seed)
+        I = torch.from_numpy(pairs[0][0]).pin_memory()
+        Is = [I] * len(tiles)
+        Js = [torch.from_numpy(J).pin_memory() for _, J in pairs]
+        return Is, Js
+    Is = [torch.empty((t.H, t.W), dtype=torch.uint8).pin_memory() for t in tiles]
+    Js = [torch.empty((t.H, t.W), dtype=torch.uint8).pin_memory() for t in tiles]
+    synth.generate_into(tiles, w.seed, [x.data_ptr() for x in Is], [x.data_ptr() for x in Js])
+    return Is, Js
+
+
+def cpu_baseline(w, tiles, shared_mask, budget_tiles=None):
+    """The CPU oracle (sweeps to stability), as it stands, on host threads."""
+    import oracle
+    import synth
+    sample = tiles if budget_tiles is None else tiles[:budget_tiles]
+    pairs = synth.generate(sample, w.seed)
+    t0 = time.perf_counter()
+    _, used = oracle.recon_tiles(pairs, [t.conn for t in sample], "sweep", nthreads=len(sample))
+    dt = time.perf_counter() - t0
+    px = sum(t.H * t.W for t in sample)
+    return px, dt, used, "%d of %d tiles (%s), full size" % (len(sample), len(tiles), w.name)
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed as the reference arm."""
+    import oracle
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, tiles, shared = workload_tiles(args.workload)
+    # one step = one tile of the workload, rotating through the tiles, each
+    # reconstructed in full by the oracle on one host thread
+    pairs = synth.generate(tiles, w.seed) if len(tiles) <= 8 else None
+    def step(i):
+        t = tiles[i % len(tiles)]
+        I, J = pairs[i % len(tiles)] if pairs else synth.tile_pair(t, w.seed)
+        t0 = time.perf_counter()
+        oracle.recon(I, J, t.conn)
+        return time.perf_counter() - t0, t.H * t.W
+    for i in range(args.warmup):
+        step(i)
+    tot_t, tot_px = 0.0, 0
+    for i in range(args.steps):
+        dt, px = step(args.warmup + i)
+        tot_t += dt
+        tot_px += px
+    v = tot_px / tot_t / 1e6
+    line = {"impl": "reference", "metric": "reconstructed Mpix/s", "value": round(v, 3),
+            "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * tot_t / max(args.steps, 1), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": w.name, "step": "one tile per step, rotating", "conn": "per tile"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                             "sample": "one full tile per step, rotating through the %d tiles" % len(tiles)},
+            "e2e": {"value": round(v, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_fn(fn, stream, J, J0, flush, reps=3):
+    """Median device time (ms) of fn() over reps runs, J reset before each."""
+    import torch
+    out = []
+    for i in range(reps + 1):
+        with torch.cuda.stream(stream):
+            for a, b in zip(J, J0):
+                a.copy_(b, non_blocking=True)
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        if i > 0:
+            out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def compare_schedules(rc, ctx, stream, Is, Js, J0, tiles, desc, px, flush, args):
+    """Batched persistent launch vs a per-tile launch loop, and the learned
+    schedule vs the plain one, on the same tiles and GPU (outputs identical:
+    R is unique; the tests check it)."""
+    res = {}
+    def batched():
+        rc.check(rc.recon_batch(ctx, desc), "batch")
+    def loop():
+        for d in desc:
+            st = rc.recon_run(ctx, d[0], d[1], d[2], d[3], d[5])
+            if st != rc.RECON_OK:
+                raise rc.ReconError(st, "recon_run")
+    res["batched_plain_mpix_s"] = round(px / time_fn(batched, stream, Js, J0, flush) / 1e3, 1)
+    res["per_tile_loop_mpix_s"] = round(px / time_fn(loop, stream, Js, J0, flush, reps=2) / 1e3, 1)
+    try:
+        from paper_1311_0378_gb300 import cost_model
+        meta = cost_model.install(ctx)
+        st, var, order, pred = rc.recon_sched_plan_batch(ctx, desc)
+        rc.check(st, "plan")
+        def learned():
+            rc.check(rc.recon_batch_ex(ctx, desc, var, order), "learned batch")
+        def learned_full():   # planning (features + MLP) inside the timed region
+            st2, v2, o2, _ = rc.recon_sched_plan_batch(ctx, desc)
+            rc.check(st2, "plan")
+            rc.check(rc.recon_batch_ex(ctx, desc, v2, o2), "learned batch")
+        res["batched_learned_mpix_s"] = round(px / time_fn(learned, stream, Js, J0, flush) / 1e3, 1)
+        res["batched_learned_with_planning_mpix_s"] = round(px / time_fn(learned_full, stream, Js, J0, flush) / 1e3, 1)
+        res["learned_variant_b_fraction"] = round(sum(1 for v in var if v != -1) / len(var), 3)
+        res["model_tiles"] = meta.get("tiles")
+    except (OSError, ValueError) as e:
+        res["batched_learned_mpix_s"] = None
+        res["learned_note"] = "no trained model: %s" % e
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="single4096",
+                    choices=["single4096", "single512", "batch64", "uneven1000"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--block-h", type=int, default=0)
+    ap.add_argument("--sweeps", type=int, default=-99)
+    ap.add_argument("--bands", type=int, default=0)
+    ap.add_argument("--compare", action="store_true",
+                    help="also time the per-tile launch loop and the learned schedule")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1311_0378_gb300 as rc
+    from paper_1311_0378_gb300 import build as rbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        rbuild.build()
+    if dist:
+        dist.barrier()
+
+    w, tiles, shared = workload_tiles(args.workload)
+    Is_h, Js_h = gen_host(w, tiles, shared)
+    dev = torch.device("cuda", local)
+    if shared:
+        Id = Is_h[0].to(dev)
+        Is = [Id] * len(tiles)
+    else:
+        Is = [x.to(dev) for x in Is_h]
+    J0 = [x.to(dev) for x in Js_h]
+    Js = [x.clone() for x in J0]
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.Stream(device=dev)
+    ctx = rc.recon_init(local, stream.cuda_stream, 0)
+    for key, val in ((rc.RECON_P_BLOCK_H, args.block_h), (rc.RECON_P_BANDS, args.bands)):
+        if val:
+            rc.check(rc.recon_set_param(ctx, key, val))
+    if args.sweeps != -99:
+        rc.check(rc.recon_set_param(ctx, rc.RECON_P_SWEEPS, args.sweeps))
+    desc = [(I.data_ptr(), J.data_ptr(), t.H, t.W, t.W, t.conn) for I, J, t in zip(Is, Js, tiles)]
+    tuned = None
+    if args.autotune:
+        st, tuned = rc.recon_autotune(ctx, desc, 2)
+        rc.check(st, "recon_autotune")
+    params = {"block_h": rc.recon_get_param(ctx, rc.RECON_P_BLOCK_H),
+              "bands": rc.recon_get_param(ctx, rc.RECON_P_BANDS),
+              "scan_pairs": rc.recon_get_param(ctx, rc.RECON_P_SWEEPS),
+              "grid": rc.recon_get_param(ctx, rc.RECON_P_GRID), "autotuned": tuned is not None}
+    px = sum(t.H * t.W for t in tiles)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        with torch.cuda.stream(stream):
+            for J, J0_ in zip(Js, J0):
+                J.copy_(J0_, non_blocking=True)
+        st = rc.recon_batch(ctx, desc)
+        if st != rc.RECON_OK:
+            raise rc.ReconError(st, "recon_batch")
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    rc.check(rc.recon_sync(ctx), "warmup")
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms = []
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            stream.synchronize()
+            kern_ms.append(rc.recon_last_kernel_ms(ctx))
+        torch.cuda.synchronize()
+    rc.check(rc.recon_sync(ctx), "timed steps")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * px / (ms / 1e3) / 1e6
+
+    compare = None
+    if args.compare and len(tiles) > 1:
+        compare = compare_schedules(rc, ctx, stream, Is, Js, J0, tiles, desc, px, flush, args)
+
+    # end to end: host (pinned) buffers through recon_batch_host
+    Jh = [x.clone().pin_memory() for x in Js_h]
+    htiles = [(I.data_ptr(), J.data_ptr(), t.H, t.W, t.W, t.conn) for I, J, t in zip(Is_h, Jh, tiles)]
+    e2e_ms = []
+    for i in range(args.e2e_steps + 1):
+        for a, b in zip(Jh, Js_h):
+            a.copy_(b)
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc.check(rc.recon_batch_host(ctx, htiles), "recon_batch_host")
+        if i > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e = world * px / (statistics.median(e2e_ms) / 1e3) / 1e6
+    h2d = sum(2 * t.H * t.W for t in tiles)
+    d2h = px
+    rc.recon_free(ctx)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    pk, src = peaks()
+    kms = statistics.mean(kern_ms)
+    achieved = ALG_BYTES_PER_PX * px / (kms / 1e3) / 1e9
+    line = {
+        "metric": "reconstructed Mpix/s", "value": round(value, 2), "unit": "Mpix/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "tiles": len(tiles), "pixels_per_step": px,
+                   "conn": sorted({t.conn for t in tiles}), "markers": "h-dome + fill-holes",
+                   "l2": "flushed before each timed step (512 MiB write)", "bit_exact": "see tests -m gpu",
+                   **params},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(achieved / pk["hbm_gbs"], 5), "traffic": None,
+                     "kernel": "recon_persistent", "kernel_ms": round(kms, 4),
+                     "alg_bytes_per_px": ALG_BYTES_PER_PX, "peak_source": src},
+        "e2e": {"value": round(e2e, 2), "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "compare": compare,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
+        cpx, cdt, used, sample = cpu_baseline(w, tiles, shared, None if len(tiles) <= 8 else 4)
+        line["cpu_baseline"] = {"value": round(cpx / cdt / 1e6, 3), "unit": "Mpix/s", "cores": used,
+                                "kind": "oracle", "sample": sample, "seconds": round(cdt, 2)}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

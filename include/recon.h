@@ -1,0 +1,200 @@
+/*
+ * recon.h -- C ABI of the GB300 (sm_103a) grayscale morphological
+ * reconstruction library.
+ *
+ * Operation (Table II, "Morphological Reconstruction": flood-fill of a marker
+ * image J limited by a mask image I, 4- or 8-connected, after Vincent 1993):
+ *     R = lim_n delta_I^n(J),   delta_I(X)(p) = min( max_{q in N(p)} X(q), I(p) ),
+ * N(p) = p and its 4 or 8 neighbours inside the image. R is computed by the
+ * irregular wavefront propagation pattern (Sec. III-B, Algorithm 1) in the
+ * hybrid form of Sec. VI-B (irregular operations): raster / anti-raster scans
+ * first, then queue-driven propagation. R is unique, so every schedule returns
+ * the same bytes.
+ *
+ * Images are uint8, row-major, `pitch` bytes between rows (pitch >= W). All
+ * image pointers handed to recon_run / recon_batch are DEVICE pointers owned by
+ * the caller; J is read as the marker and overwritten in place with R (as D is
+ * updated in place in Algorithm 1). The library owns only its scratch memory.
+ *
+ * Calls are asynchronous on the context's stream: the return value is the
+ * argument-check status; the device status (marker check, bounded waits) is
+ * returned by recon_sync, or at once when the context has RECON_FLAG_SYNC.
+ * No function aborts, traps or spins without a bound; errors are status codes.
+ * A context is used by one host thread at a time.
+ */
+#ifndef RECON_H
+#define RECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct recon_ctx recon_ctx;
+
+/* Status codes. */
+enum {
+    RECON_OK = 0,
+    RECON_EINVAL = 1,    /* bad argument (null pointer, size, conn not 4/8, pitch < W) */
+    RECON_EMARKER = 2,   /* J > I at some pixel: the precondition J <= I does not hold.
+                            J of that tile is then left in an unspecified state. */
+    RECON_ENOMEM = 3,    /* device or host allocation failed */
+    RECON_ECUDA = 4,     /* a CUDA runtime call failed */
+    RECON_ETIMEOUT = 5   /* a bounded device-side wait ran out; outputs unspecified */
+};
+
+/* Flags for recon_init. */
+#define RECON_FLAG_SYNC      0x1u  /* each call waits for the device and returns its status */
+#define RECON_FLAG_NO_CHECK  0x2u  /* skip the J <= I check (caller guarantees it) */
+#define RECON_FLAG_LEARNED   0x4u  /* recon_batch: the cost model picks variant and order */
+#define RECON_FLAG_NO_GRAPH  0x8u  /* recon_batch: never capture / replay a CUDA graph */
+
+/* One tile of a batch: device pointers, caller-owned. */
+typedef struct {
+    const uint8_t *I;   /* mask, H x W, row stride `pitch` bytes */
+    uint8_t *J;         /* marker in, R out (in place) */
+    int H, W, pitch;    /* H, W >= 1; pitch >= W */
+    int conn;           /* 4 or 8 */
+} recon_tile;
+
+/* Creates a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
+ * (NULL: the context creates its own non-blocking stream). flags: RECON_FLAG_*.
+ * Returns RECON_OK and *ctx, or an error code with *ctx = NULL. */
+int recon_init(recon_ctx **ctx, int device, void *cuda_stream, unsigned flags);
+
+/* Reconstructs one tile (Table II; Algorithm 1 with the hybrid scan + queue
+ * schedule of Sec. VI-B). I, J: device pointers, pitch = W. J <- R in place. */
+int recon_run(recon_ctx *ctx, const uint8_t *I, uint8_t *J, int H, int W, int conn);
+
+/* Reconstructs n independent tiles of any sizes in one persistent launch
+ * (tiles are processed concurrently, as the 4K x 4K tiles of Sec. V are).
+ * `tiles` is a HOST array of n descriptors with device image pointers.
+ * Tiles must not overlap in memory. With RECON_FLAG_LEARNED the cost model
+ * chooses each tile's variant and the packing order (never the pixel values).
+ * On a device error, recon_last_error_tile names the first failing tile. */
+int recon_batch(recon_ctx *ctx, const recon_tile *tiles, int n);
+
+/* As recon_batch with an explicit schedule: variant[t] = number of raster +
+ * anti-raster pairs a block runs on its first visit before its queue phase
+ * (-1 = scans to stability, no queue), order[] = permutation of 0..n-1 giving
+ * the packing order. Either array may be NULL (context defaults). */
+int recon_batch_ex(recon_ctx *ctx, const recon_tile *tiles, int n, const int *variant,
+                   const int *order);
+
+/* End-to-end form: I, J are HOST pointers (pinned or pageable), pitch = W.
+ * Copies in, reconstructs, copies R back into J, and waits. */
+int recon_run_host(recon_ctx *ctx, const uint8_t *I, uint8_t *J, int H, int W, int conn);
+
+/* End-to-end batch: tiles[].I / tiles[].J are HOST pointers; waits. */
+int recon_batch_host(recon_ctx *ctx, const recon_tile *tiles, int n);
+
+/* Waits for the context's stream; returns the device status of the last call. */
+int recon_sync(recon_ctx *ctx);
+
+/* Index of the first tile of the last batch that failed, or -1. Syncs. */
+int recon_last_error_tile(recon_ctx *ctx);
+
+/* Frees the context and its scratch memory (syncs first). NULL is accepted. */
+int recon_free(recon_ctx *ctx);
+
+/* Static description of a status code. */
+const char *recon_strerror(int status);
+
+/* Tunables (recon_set_param / recon_get_param). */
+enum {
+    RECON_P_BLOCK_H = 1,     /* block height in rows: 32, 64 or 128 (block width is 128) */
+    RECON_P_SWEEPS = 2,      /* default variant: scan pairs before the queue; -1 = scans only */
+    RECON_P_GRID = 3,        /* CTAs of the persistent launch; 0 = SMs x occupancy */
+    RECON_P_BANDS = 4,       /* warps that scan a block concurrently (1, 2 or 4) */
+    RECON_P_WAIT_NS = 5,     /* limit of one device-side idle wait, ns (default 2e9) */
+    RECON_P_ORDER = 6,       /* default packing order: 0 = as given, 1 = largest area first */
+    RECON_P_TEST_STALL = 7,  /* testing: 1 = add a phantom unit of work that never ends,
+                                so the bounded wait must run out (RECON_ETIMEOUT) */
+    RECON_P_TMA = 8          /* 1 (default): tiles whose rows and bases are 16-byte aligned
+                                are loaded into shared memory by TMA; 0 = plain loads */
+};
+int recon_set_param(recon_ctx *ctx, int key, int64_t value);
+int64_t recon_get_param(recon_ctx *ctx, int key);
+
+/* Work counters of one tile in the last call (propagation work measured by
+ * the method itself: what the cost model learns from). */
+typedef struct {
+    uint64_t visits;      /* block visits (first visits + revisits after a halo change) */
+    uint64_t scan_rows;   /* rows processed by raster / anti-raster scans */
+    uint64_t pops;        /* queue entries processed */
+    uint64_t seeds;       /* seeding passes over a block */
+} recon_work;
+
+/* Copies the counters of the last call's first n tiles into out[] (syncs). */
+int recon_get_work(recon_ctx *ctx, recon_work *out, int n);
+
+/* Device time of the last call's persistent kernel in ms (CUDA events on the
+ * context's stream; syncs). */
+int recon_last_kernel_ms(recon_ctx *ctx, float *ms);
+
+
+/* Autotuner: times every candidate block height {32, 64, 128} x bands
+ * {1, 2, 4} x first-visit scan pairs {0, 1, 2} on this batch (each `reps`
+ * times after one warm-up run, J restored from a device backup before every
+ * run), installs the fastest in the context and writes it to best[3] =
+ * {block height, bands, scan pairs}. J holds its original marker on return.
+ * The paper tunes its scan-to-queue switch point the same way (Sec. VI-B). */
+int recon_autotune(recon_ctx *ctx, const recon_tile *tiles, int n, int reps, int *best);
+
+/* ---- learned cost model ------------------------------------------------
+ * The scheduler's analogue of the paper's performance-aware task scheduling
+ * (Sec. IV, PATS: per-task speedup estimates choose where each task runs):
+ * a multilayer perceptron 20 -> 64 -> 64 -> 2 (ReLU, fp32) maps per-tile
+ * features to the predicted log cost of two variants; the scheduler gives each
+ * tile its cheaper variant and packs tiles by decreasing predicted cost. It
+ * only reorders and re-parameterises work; pixel values are never touched.
+ * All float pointers below are DEVICE pointers owned by the caller, in the
+ * flat parameter layout W1 (64x20), b1 (64), W2 (64x64), b2 (64), W3 (2x64),
+ * b3 (2), row-major. */
+#define RECON_NFEAT 20
+#define RECON_MLP_NPARAMS 5634
+
+/* Features of n tiles into feat (n x 20 fp32): [0..15] fraction of pixels with
+ * (I - J) >> 4 == k, [16] fraction with I >= 100 (blob pixels), [17] fraction
+ * with J == 0, [18] log2(H) / 12, [19] log2(W) / 12. One pass over I and J. Syncs. */
+int recon_features(recon_ctx *ctx, const recon_tile *tiles, int n, float *feat);
+
+/* Y (n x 2) = MLP(theta, X (n x 20)). */
+int recon_mlp_forward(recon_ctx *ctx, const float *theta, const float *X, int n, float *Y);
+
+/* Adds to grad (5634 floats) the gradient of L = 1/(2n) sum (Y - T)^2 over the
+ * samples idx[0..n) (idx NULL: 0..n-1) and, when loss is not NULL, adds L to
+ * *loss. The caller zeroes grad and loss first. */
+int recon_mlp_grad(recon_ctx *ctx, const float *theta, const float *X, const float *T, const int *idx,
+                   int n, float *grad, float *loss);
+
+/* One Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8), step
+ * number t >= 1; grad is zeroed afterwards. */
+int recon_mlp_adam(recon_ctx *ctx, float *theta, float *grad, float *m, float *v, int t, float lr);
+
+/* Mini-batch Adam for `epochs` epochs over X (n x 20), T (n x 2), shuffled per
+ * epoch by a SplitMix64-driven Fisher-Yates permutation of (seed, epoch).
+ * epoch_loss (HOST, optional, `epochs` floats) receives each epoch's mean batch
+ * loss. Syncs. */
+int recon_mlp_train(recon_ctx *ctx, float *theta, const float *X, const float *T, int n, int epochs,
+                    int batch, float lr, uint64_t seed, float *epoch_loss);
+
+/* Installs a trained model for RECON_FLAG_LEARNED batches. theta and norm are
+ * HOST pointers: norm = (mean_a, std_a, mean_b, std_b) de-normalising the two
+ * outputs; variant_a / variant_b are the variants (as in recon_batch_ex) that
+ * outputs 0 and 1 predict. */
+int recon_sched_set_model(recon_ctx *ctx, const float *theta, const float *norm, int variant_a,
+                          int variant_b);
+
+/* The plan the model makes for a batch (HOST outputs): variant[n], order[n]
+ * and, optionally, pred[2n] (predicted log costs). Syncs. */
+int recon_sched_plan_batch(recon_ctx *ctx, const recon_tile *tiles, int n, int *variant, int *order,
+                           float *pred);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECON_H */

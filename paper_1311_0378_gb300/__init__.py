@@ -1,0 +1,236 @@
+"""Python binding of librecon.so, the GB300 grayscale morphological
+reconstruction library (C ABI in include/recon.h).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels behind the C ABI. Functions keep the C names; image arguments are
+device addresses (ints, e.g. ``tensor.data_ptr()`` of contiguous uint8 CUDA
+tensors), except in the ``*_host`` entry points, which take host addresses.
+There is no fallback: if librecon.so is missing or fails to load, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librecon.so")
+
+RECON_OK, RECON_EINVAL, RECON_EMARKER, RECON_ENOMEM, RECON_ECUDA, RECON_ETIMEOUT = range(6)
+RECON_FLAG_SYNC, RECON_FLAG_NO_CHECK, RECON_FLAG_LEARNED, RECON_FLAG_NO_GRAPH = 1, 2, 4, 8
+(RECON_P_BLOCK_H, RECON_P_SWEEPS, RECON_P_GRID, RECON_P_BANDS, RECON_P_WAIT_NS, RECON_P_ORDER,
+ RECON_P_TEST_STALL, RECON_P_TMA) = range(1, 9)
+
+# every symbol the header declares; tests check the library exports them all
+SYMBOLS = ("recon_init", "recon_run", "recon_batch", "recon_batch_ex", "recon_run_host",
+           "recon_batch_host", "recon_sync", "recon_last_error_tile", "recon_free",
+           "recon_strerror", "recon_set_param", "recon_get_param", "recon_get_work",
+           "recon_last_kernel_ms", "recon_features", "recon_mlp_forward", "recon_mlp_grad",
+           "recon_mlp_adam", "recon_mlp_train", "recon_sched_set_model", "recon_sched_plan_batch",
+           "recon_autotune")
+RECON_NFEAT, RECON_MLP_NPARAMS = 20, 5634
+
+
+class recon_tile(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_void_p), ("J", ctypes.c_void_p), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("pitch", ctypes.c_int), ("conn", ctypes.c_int)]
+
+
+class recon_work(ctypes.Structure):
+    _fields_ = [("visits", ctypes.c_uint64), ("scan_rows", ctypes.c_uint64),
+                ("pops", ctypes.c_uint64), ("seeds", ctypes.c_uint64)]
+
+
+class ReconError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what or "recon", recon_strerror(status), status))
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads librecon.so (built by __graft_entry__.build() or
+    paper_1311_0378_gb300.build). Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("librecon.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, u, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_int64
+    tp = ctypes.POINTER(recon_tile)
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "recon_init": ([ctypes.POINTER(vp), i, vp, u], i),
+        "recon_run": ([vp, vp, vp, i, i, i], i),
+        "recon_batch": ([vp, tp, i], i),
+        "recon_batch_ex": ([vp, tp, i, ip, ip], i),
+        "recon_run_host": ([vp, vp, vp, i, i, i], i),
+        "recon_batch_host": ([vp, tp, i], i),
+        "recon_sync": ([vp], i),
+        "recon_last_error_tile": ([vp], i),
+        "recon_free": ([vp], i),
+        "recon_strerror": ([i], ctypes.c_char_p),
+        "recon_set_param": ([vp, i, i64], i),
+        "recon_get_param": ([vp, i], i64),
+        "recon_get_work": ([vp, ctypes.POINTER(recon_work), i], i),
+        "recon_last_kernel_ms": ([vp, ctypes.POINTER(ctypes.c_float)], i),
+        "recon_features": ([vp, tp, i, vp], i),
+        "recon_mlp_forward": ([vp, vp, vp, i, vp], i),
+        "recon_mlp_grad": ([vp, vp, vp, vp, vp, i, vp, vp], i),
+        "recon_mlp_adam": ([vp, vp, vp, vp, vp, i, ctypes.c_float], i),
+        "recon_mlp_train": ([vp, vp, vp, vp, i, i, i, ctypes.c_float, ctypes.c_uint64, vp], i),
+        "recon_sched_set_model": ([vp, vp, vp, i, i], i),
+        "recon_sched_plan_batch": ([vp, tp, i, vp, vp, vp], i),
+        "recon_autotune": ([vp, tp, i, i, vp], i),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _tiles(tiles: Sequence[Tuple[int, int, int, int, int, int]]):
+    arr = (recon_tile * max(len(tiles), 1))()
+    for k, (I, J, H, W, pitch, conn) in enumerate(tiles):
+        arr[k] = recon_tile(I, J, H, W, pitch, conn)
+    return arr
+
+
+def _ints(v):
+    if v is None:
+        return None
+    return (ctypes.c_int * max(len(v), 1))(*[int(x) for x in v])
+
+
+def recon_init(device: int = 0, stream: int = 0, flags: int = 0) -> ctypes.c_void_p:
+    """Creates a context; raises ReconError on failure. `stream` is a
+    cudaStream_t address (0: the context makes its own)."""
+    ctx = ctypes.c_void_p()
+    rc = lib().recon_init(ctypes.byref(ctx), device, ctypes.c_void_p(stream or None), flags)
+    if rc != RECON_OK:
+        raise ReconError(rc, "recon_init")
+    return ctx
+
+
+def recon_run(ctx, I: int, J: int, H: int, W: int, conn: int) -> int:
+    return lib().recon_run(ctx, I, J, H, W, conn)
+
+
+def recon_batch(ctx, tiles) -> int:
+    """tiles: sequence of (I, J, H, W, pitch, conn) with device addresses."""
+    return lib().recon_batch(ctx, _tiles(tiles), len(tiles))
+
+
+def recon_batch_ex(ctx, tiles, variant=None, order=None) -> int:
+    return lib().recon_batch_ex(ctx, _tiles(tiles), len(tiles), _ints(variant), _ints(order))
+
+
+def recon_run_host(ctx, I: int, J: int, H: int, W: int, conn: int) -> int:
+    return lib().recon_run_host(ctx, I, J, H, W, conn)
+
+
+def recon_batch_host(ctx, tiles) -> int:
+    """tiles: sequence of (I, J, H, W, pitch, conn) with HOST addresses."""
+    return lib().recon_batch_host(ctx, _tiles(tiles), len(tiles))
+
+
+def recon_sync(ctx) -> int:
+    return lib().recon_sync(ctx)
+
+
+def recon_last_error_tile(ctx) -> int:
+    return lib().recon_last_error_tile(ctx)
+
+
+def recon_free(ctx) -> int:
+    return lib().recon_free(ctx)
+
+
+def recon_strerror(status: int) -> str:
+    return lib().recon_strerror(status).decode()
+
+
+def recon_set_param(ctx, key: int, value: int) -> int:
+    return lib().recon_set_param(ctx, key, value)
+
+
+def recon_get_param(ctx, key: int) -> int:
+    return lib().recon_get_param(ctx, key)
+
+
+def recon_get_work(ctx, n: int):
+    out = (recon_work * max(n, 1))()
+    rc = lib().recon_get_work(ctx, out, n)
+    if rc != RECON_OK:
+        raise ReconError(rc, "recon_get_work")
+    return [dict(visits=w.visits, scan_rows=w.scan_rows, pops=w.pops, seeds=w.seeds) for w in out[:n]]
+
+
+def recon_last_kernel_ms(ctx) -> float:
+    ms = ctypes.c_float()
+    rc = lib().recon_last_kernel_ms(ctx, ctypes.byref(ms))
+    if rc != RECON_OK:
+        raise ReconError(rc, "recon_last_kernel_ms")
+    return ms.value
+
+
+def check(rc: int, what: str = "") -> None:
+    """Raises ReconError unless rc == RECON_OK."""
+    if rc != RECON_OK:
+        raise ReconError(rc, what)
+
+
+# ---- learned cost model (device float pointers as ints) ----
+
+def recon_features(ctx, tiles, feat: int) -> int:
+    return lib().recon_features(ctx, _tiles(tiles), len(tiles), feat)
+
+
+def recon_mlp_forward(ctx, theta: int, X: int, n: int, Y: int) -> int:
+    return lib().recon_mlp_forward(ctx, theta, X, n, Y)
+
+
+def recon_mlp_grad(ctx, theta: int, X: int, T: int, idx: int, n: int, grad: int, loss: int) -> int:
+    return lib().recon_mlp_grad(ctx, theta, X, T, idx or None, n, grad, loss or None)
+
+
+def recon_mlp_adam(ctx, theta: int, grad: int, m: int, v: int, t: int, lr: float) -> int:
+    return lib().recon_mlp_adam(ctx, theta, grad, m, v, t, lr)
+
+
+def recon_mlp_train(ctx, theta: int, X: int, T: int, n: int, epochs: int, batch: int, lr: float,
+                    seed: int = 0):
+    """Returns (status, [mean batch loss per epoch])."""
+    losses = (ctypes.c_float * epochs)()
+    rc = lib().recon_mlp_train(ctx, theta, X, T, n, epochs, batch, lr, seed, losses)
+    return rc, list(losses)
+
+
+def recon_sched_set_model(ctx, theta_host: Sequence[float], norm: Sequence[float], variant_a: int,
+                          variant_b: int) -> int:
+    th = (ctypes.c_float * RECON_MLP_NPARAMS)(*[float(x) for x in theta_host])
+    nm = (ctypes.c_float * 4)(*[float(x) for x in norm])
+    return lib().recon_sched_set_model(ctx, th, nm, variant_a, variant_b)
+
+
+def recon_sched_plan_batch(ctx, tiles):
+    """Returns (status, variant[n], order[n], pred[2n])."""
+    n = len(tiles)
+    v = (ctypes.c_int * n)()
+    o = (ctypes.c_int * n)()
+    p = (ctypes.c_float * (2 * n))()
+    rc = lib().recon_sched_plan_batch(ctx, _tiles(tiles), n, v, o, p)
+    return rc, list(v), list(o), list(p)
+
+
+def recon_autotune(ctx, tiles, reps: int = 2):
+    """Returns (status, (block_h, bands, scan_pairs)) and installs the best."""
+    best = (ctypes.c_int * 3)()
+    rc = lib().recon_autotune(ctx, _tiles(tiles), len(tiles), reps, best)
+    return rc, tuple(best)

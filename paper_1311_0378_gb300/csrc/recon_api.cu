@@ -1,0 +1,775 @@
+// Host side of the C ABI declared in include/recon.h: argument checks, scratch
+// management, the launch of the persistent reconstruction kernel, CUDA-graph
+// replay of repeated batches, and the end-to-end (host buffer) entry points.
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+#include <algorithm>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "recon.h"
+#include "recon_internal.h"
+#include "recon_sched.h"
+#include "recon_learn.h"
+
+extern "C" size_t rk_smem_bytes(int bh);
+extern "C" cudaError_t rk_configure(int bh, int *ctas_per_sm);
+extern "C" cudaError_t rk_launch_init(int grid, const rk::Params *P, cudaStream_t st);
+extern "C" cudaError_t rk_launch_main(int bh, int grid, const rk::Params *P, cudaStream_t st);
+
+struct recon_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    unsigned flags = 0;
+    int sms = 0;
+    // tunables
+    int bh = 64, k = 1, grid = 0, bands = 4, order_policy = 1, phantom = 0, use_tma = 1;
+    long long wait_ns = 2000000000ll;
+    // device scratch
+    unsigned char *d_meta = nullptr; size_t cap_meta = 0;      // descriptors + order tables
+    unsigned *d_state = nullptr, *d_ring = nullptr; size_t cap_blocks = 0;
+    rk::Ctl *d_ctl = nullptr;
+    int *d_tile_err = nullptr; rk::Work *d_work = nullptr; size_t cap_tiles = 0;
+    uint16_t *d_spill = nullptr; size_t cap_spill_ctas = 0;
+    // host staging (pinned)
+    unsigned char *h_meta = nullptr; size_t cap_hmeta = 0;
+    cudaEvent_t meta_free = nullptr, ev0 = nullptr, ev1 = nullptr;
+    // end-to-end buffers
+    uint8_t *d_img = nullptr; size_t cap_img = 0;
+    // last call
+    int last_n = 0;
+    int launched = 0;
+    int last_err_tile = -1;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gsig;
+    // learned scheduler
+    recon_sched *sched = nullptr;
+};
+
+static int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return RECON_OK;
+    if (e == cudaErrorMemoryAllocation) return RECON_ENOMEM;
+    return RECON_ECUDA;
+}
+
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return cuda_status(e_); } while (0)
+
+template <typename T>
+static int grow(T **p, size_t *cap, size_t need)
+{
+    if (*cap >= need && *p) return RECON_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t n = std::max(need, (size_t)1);
+    CK(cudaMalloc((void **)p, n * sizeof(T)));
+    *cap = n;
+    return RECON_OK;
+}
+
+static void drop_graph(recon_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gsig.clear();
+}
+
+extern "C" int recon_init(recon_ctx **out, int device, void *cuda_stream, unsigned flags)
+{
+    if (!out) return RECON_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return RECON_EINVAL;
+    CK(cudaSetDevice(device));
+    recon_ctx *c = new (std::nothrow) recon_ctx();
+    if (!c) return RECON_ENOMEM;
+    c->device = device;
+    c->flags = flags;
+    cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            c->stream = (cudaStream_t)cuda_stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->meta_free, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctl, sizeof(rk::Ctl));
+    if (e == cudaSuccess) {
+        int occ = 0;
+        for (int bh : {32, 64, 128})
+            if (e == cudaSuccess) e = rk_configure(bh, &occ);
+    }
+    if (e != cudaSuccess) {
+        recon_free(c);
+        return cuda_status(e);
+    }
+    c->sched = recon_sched_create();
+    *out = c;
+    return RECON_OK;
+}
+
+extern "C" int recon_free(recon_ctx *c)
+{
+    if (!c) return RECON_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    cudaFree(c->d_meta);
+    cudaFree(c->d_state);
+    cudaFree(c->d_ring);
+    cudaFree(c->d_ctl);
+    cudaFree(c->d_tile_err);
+    cudaFree(c->d_work);
+    cudaFree(c->d_spill);
+    cudaFree(c->d_img);
+    if (c->h_meta) cudaFreeHost(c->h_meta);
+    if (c->meta_free) cudaEventDestroy(c->meta_free);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    recon_sched_destroy(c->sched);
+    delete c;
+    return RECON_OK;
+}
+
+extern "C" const char *recon_strerror(int s)
+{
+    switch (s) {
+    case RECON_OK: return "ok";
+    case RECON_EINVAL: return "invalid argument";
+    case RECON_EMARKER: return "marker exceeds mask (J > I) at some pixel";
+    case RECON_ENOMEM: return "out of memory";
+    case RECON_ECUDA: return "CUDA runtime error";
+    case RECON_ETIMEOUT: return "bounded device wait ran out";
+    }
+    return "unknown status";
+}
+
+static int tile_ok(const recon_tile &t)
+{
+    if (!t.I || !t.J || t.H < 1 || t.W < 1 || t.pitch < t.W) return 0;
+    if (t.conn != 4 && t.conn != 8) return 0;
+    if ((double)t.H * (double)t.pitch > 9.0e18) return 0;
+    return 1;
+}
+
+extern "C" int recon_set_param(recon_ctx *c, int key, int64_t v)
+{
+    if (!c) return RECON_EINVAL;
+    switch (key) {
+    case RECON_P_BLOCK_H:
+        if (v != 32 && v != 64 && v != 128) return RECON_EINVAL;
+        c->bh = (int)v; break;
+    case RECON_P_SWEEPS:
+        if (v < -1 || v > 64) return RECON_EINVAL;
+        c->k = (int)v; break;
+    case RECON_P_GRID:
+        if (v < 0 || v > (1 << 20)) return RECON_EINVAL;
+        c->grid = (int)v; break;
+    case RECON_P_BANDS:
+        if (v != 1 && v != 2 && v != 4) return RECON_EINVAL;
+        c->bands = (int)v; break;
+    case RECON_P_WAIT_NS:
+        if (v < 1000 || v > 600000000000ll) return RECON_EINVAL;
+        c->wait_ns = v; break;
+    case RECON_P_ORDER:
+        if (v != 0 && v != 1) return RECON_EINVAL;
+        c->order_policy = (int)v; break;
+    case RECON_P_TEST_STALL:
+        if (v != 0 && v != 1) return RECON_EINVAL;
+        c->phantom = (int)v; break;
+    case RECON_P_TMA:
+        if (v != 0 && v != 1) return RECON_EINVAL;
+        c->use_tma = (int)v; break;
+    default: return RECON_EINVAL;
+    }
+    drop_graph(c);
+    return RECON_OK;
+}
+
+extern "C" int64_t recon_get_param(recon_ctx *c, int key)
+{
+    if (!c) return -1;
+    switch (key) {
+    case RECON_P_BLOCK_H: return c->bh;
+    case RECON_P_SWEEPS: return c->k;
+    case RECON_P_GRID: {
+        if (c->grid) return c->grid;
+        int occ = 0;
+        if (rk_configure(c->bh, &occ) != cudaSuccess) return -1;
+        return (int64_t)occ * c->sms;
+    }
+    case RECON_P_BANDS: return c->bands;
+    case RECON_P_WAIT_NS: return c->wait_ns;
+    case RECON_P_ORDER: return c->order_policy;
+    case RECON_P_TEST_STALL: return c->phantom;
+    case RECON_P_TMA: return c->use_tma;
+    }
+    return -1;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against libcuda needed).
+typedef CUresult (*encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static encode_fn get_encode()
+{
+    static encode_fn fn = nullptr;
+    static int tried = 0;
+    if (!tried) {
+        tried = 1;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (encode_fn)p;
+    }
+    return fn;
+}
+
+// Tensor map of one uint8 image: dims (W, H), row stride pitch, box of
+// BOXW x (bh + 2) bytes; out-of-bounds elements read as zero.
+static int encode_map(CUtensorMap *m, const void *base, int H, int W, int pitch, int bh)
+{
+    encode_fn fn = get_encode();
+    if (!fn) return 0;
+    cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    cuuint32_t box[2] = {(cuuint32_t)rk::BOXW, (cuuint32_t)(bh + 2)};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct MetaLayout {
+    size_t off_order, off_base, off_maps, total;
+};
+
+static MetaLayout meta_layout(int n)
+{
+    MetaLayout L;
+    L.off_order = align_up(sizeof(rk::TileDesc) * n, 16);
+    L.off_base = align_up(L.off_order + sizeof(int) * n, 16);
+    L.off_maps = align_up(L.off_base + sizeof(unsigned) * (n + 1), 128);
+    L.total = L.off_maps + 256 * (size_t)n;
+    return L;
+}
+
+// Builds the descriptor table + packing tables in the pinned staging buffer.
+// Returns bytes used, or 0 on failure.
+static int stage_meta(recon_ctx *c, const recon_tile *tiles, int n, const int *variant,
+                      const int *order, size_t *bytes, unsigned *nblocks)
+{
+    const MetaLayout L = meta_layout(n);
+    const size_t off_order = L.off_order, off_base = L.off_base, total = L.total;
+    // the previous call's copy out of the staging buffer must be done
+    CK(cudaEventSynchronize(c->meta_free));
+    if (c->cap_hmeta < total) {
+        if (c->h_meta) cudaFreeHost(c->h_meta);
+        c->h_meta = nullptr;
+        c->cap_hmeta = 0;
+        CK(cudaMallocHost((void **)&c->h_meta, total));
+        c->cap_hmeta = total;
+    }
+    rk::TileDesc *D = (rk::TileDesc *)c->h_meta;
+    int *ord = (int *)(c->h_meta + off_order);
+    unsigned *base = (unsigned *)(c->h_meta + off_base);
+    unsigned long long nb = 0;
+    for (int t = 0; t < n; ++t) {
+        const recon_tile &T = tiles[t];
+        rk::TileDesc d;
+        memset(&d, 0, sizeof(d));
+        d.I = T.I; d.J = T.J; d.H = T.H; d.W = T.W; d.pitch = T.pitch; d.conn = T.conn;
+        d.nbx = (T.W + rk::BW - 1) / rk::BW;
+        d.nby = (T.H + c->bh - 1) / c->bh;
+        d.k = variant ? variant[t] : c->k;
+        d.fast = ((T.pitch % 4) == 0 && ((uintptr_t)T.I % 4) == 0 && ((uintptr_t)T.J % 4) == 0) ? 1 : 0;
+        CUtensorMap *maps = (CUtensorMap *)(c->h_meta + L.off_maps + 256 * (size_t)t);
+        memset(maps, 0, 256);
+        if (c->use_tma && (T.pitch % 16) == 0 && ((uintptr_t)T.I % 16) == 0 && ((uintptr_t)T.J % 16) == 0 &&
+            encode_map(&maps[0], T.I, T.H, T.W, T.pitch, c->bh) && encode_map(&maps[1], T.J, T.H, T.W, T.pitch, c->bh))
+            d.fast = 2;
+        d.block_base = (unsigned)nb;
+        nb += (unsigned long long)d.nbx * (unsigned long long)d.nby;
+        if (nb >= 0xFFFFFFF0ull) return RECON_EINVAL;
+        D[t] = d;
+    }
+    if (order) {
+        std::vector<char> seen(n, 0);
+        for (int i = 0; i < n; ++i) {
+            if (order[i] < 0 || order[i] >= n || seen[order[i]]) return RECON_EINVAL;
+            seen[order[i]] = 1;
+            ord[i] = order[i];
+        }
+    } else {
+        for (int i = 0; i < n; ++i) ord[i] = i;
+        if (c->order_policy == 1)
+            std::stable_sort(ord, ord + n, [&](int a, int b) {
+                return (long long)tiles[a].H * tiles[a].W > (long long)tiles[b].H * tiles[b].W;
+            });
+    }
+    unsigned acc = 0;
+    for (int i = 0; i < n; ++i) {
+        base[i] = acc;
+        acc += (unsigned)(D[ord[i]].nbx * D[ord[i]].nby);
+    }
+    base[n] = acc;
+    *bytes = total;
+    *nblocks = (unsigned)nb;
+    return RECON_OK;
+}
+
+static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *variant, const int *order)
+{
+    if (!c || !tiles || n < 1) return RECON_EINVAL;
+    for (int t = 0; t < n; ++t)
+        if (!tile_ok(tiles[t])) return RECON_EINVAL;
+    if (variant)
+        for (int t = 0; t < n; ++t)
+            if (variant[t] < -1 || variant[t] > 64) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+
+    std::vector<int> lv, lo;
+    if ((c->flags & RECON_FLAG_LEARNED) && !variant && !order && c->sched) {
+        int rc = recon_sched_plan(c->sched, tiles, n, c->sms, c->stream, &lv, &lo);
+        if (rc == RECON_OK) { variant = lv.data(); order = lo.data(); }
+    }
+
+    size_t bytes = 0;
+    unsigned nblocks = 0;
+    int rc = stage_meta(c, tiles, n, variant, order, &bytes, &nblocks);
+    if (rc) return rc;
+
+    int grid = c->grid;
+    if (!grid) {
+        int occ = 0;
+        CK(rk_configure(c->bh, &occ));
+        grid = std::max(1, occ) * c->sms;
+    }
+    // scratch: grow only between launches (nothing in flight uses the old buffers)
+    const bool need = c->cap_meta < bytes || c->cap_blocks < nblocks || c->cap_tiles < (size_t)n ||
+                      c->cap_spill_ctas < (size_t)grid || !c->d_state || !c->d_ring;
+    if (need) {
+        CK(cudaStreamSynchronize(c->stream));
+        drop_graph(c);
+        if ((rc = grow(&c->d_meta, &c->cap_meta, bytes))) return rc;
+        if (c->cap_blocks < nblocks || !c->d_state || !c->d_ring) {
+            size_t a = 0, b = 0;
+            if (c->d_state) cudaFree(c->d_state);
+            if (c->d_ring) cudaFree(c->d_ring);
+            c->d_state = nullptr; c->d_ring = nullptr; c->cap_blocks = 0;
+            if ((rc = grow(&c->d_state, &a, nblocks))) return rc;
+            if ((rc = grow(&c->d_ring, &b, nblocks))) return rc;
+            c->cap_blocks = std::min(a, b);
+        }
+        if (c->cap_tiles < (size_t)n || !c->d_tile_err || !c->d_work) {
+            size_t a = 0, b = 0;
+            if (c->d_tile_err) cudaFree(c->d_tile_err);
+            if (c->d_work) cudaFree(c->d_work);
+            c->d_tile_err = nullptr; c->d_work = nullptr; c->cap_tiles = 0;
+            if ((rc = grow(&c->d_tile_err, &a, (size_t)n))) return rc;
+            if ((rc = grow(&c->d_work, &b, (size_t)n))) return rc;
+            c->cap_tiles = std::min(a, b);
+        }
+        if (c->cap_spill_ctas < (size_t)grid) {
+            size_t a = 0;
+            if (c->d_spill) cudaFree(c->d_spill);
+            c->d_spill = nullptr; c->cap_spill_ctas = 0;
+            if ((rc = grow(&c->d_spill, &a, (size_t)grid * 2 * rk::GCAP))) return rc;
+            c->cap_spill_ctas = (size_t)grid;
+        }
+    }
+
+    rk::Params P;
+    memset(&P, 0, sizeof(P));
+    const MetaLayout ML = meta_layout(n);
+    P.tiles = (const rk::TileDesc *)c->d_meta;
+    P.ntiles = n;
+    P.tmaps = (const void *)(c->d_meta + ML.off_maps);
+    P.order = (const int *)(c->d_meta + ML.off_order);
+    P.order_base = (const unsigned *)(c->d_meta + ML.off_base);
+    P.nblocks = nblocks;
+    P.state = c->d_state;
+    P.ring = c->d_ring;
+    P.ctl = c->d_ctl;
+    P.tile_err = c->d_tile_err;
+    P.work = c->d_work;
+    P.spill = c->d_spill;
+    P.wait_ns = c->wait_ns;
+    P.bands = c->bands;
+    P.phantom = c->phantom;
+    P.check = (c->flags & RECON_FLAG_NO_CHECK) ? 0 : 1;
+
+    // signature of this launch: replay the captured graph when it repeats
+    std::vector<unsigned char> sig(bytes + sizeof(P) + 2 * sizeof(int));
+    memcpy(sig.data(), c->h_meta, bytes);
+    memcpy(sig.data() + bytes, &P, sizeof(P));
+    memcpy(sig.data() + bytes + sizeof(P), &grid, sizeof(int));
+    memcpy(sig.data() + bytes + sizeof(P) + sizeof(int), &c->bh, sizeof(int));
+
+    c->last_n = n;
+    c->last_err_tile = -1;
+    const bool use_graph = !(c->flags & RECON_FLAG_NO_GRAPH);
+    if (use_graph && c->gexec && sig == c->gsig) {
+        CK(cudaGraphLaunch(c->gexec, c->stream));
+        CK(cudaEventRecord(c->meta_free, c->stream));
+    } else {
+        drop_graph(c);
+        cudaGraph_t g = nullptr;
+        if (use_graph) CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemcpyAsync(c->d_meta, c->h_meta, bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = rk_launch_init(std::min(grid, 4 * c->sms), &P, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev0, c->stream);
+        if (e == cudaSuccess) e = rk_launch_main(c->bh, grid, &P, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+        if (use_graph) {
+            cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e == cudaSuccess) e = cudaGraphLaunch(c->gexec, c->stream);
+            if (e == cudaSuccess) c->gsig.swap(sig);
+            else drop_graph(c);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(c->meta_free, c->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    c->launched = 1;
+    if (c->flags & RECON_FLAG_SYNC) return recon_sync(c);
+    return RECON_OK;
+}
+
+extern "C" int recon_batch_ex(recon_ctx *c, const recon_tile *tiles, int n, const int *variant,
+                              const int *order)
+{
+    return batch_impl(c, tiles, n, variant, order);
+}
+
+extern "C" int recon_batch(recon_ctx *c, const recon_tile *tiles, int n)
+{
+    return batch_impl(c, tiles, n, nullptr, nullptr);
+}
+
+extern "C" int recon_run(recon_ctx *c, const uint8_t *I, uint8_t *J, int H, int W, int conn)
+{
+    recon_tile t;
+    t.I = I; t.J = J; t.H = H; t.W = W; t.pitch = W; t.conn = conn;
+    return batch_impl(c, &t, 1, nullptr, nullptr);
+}
+
+extern "C" int recon_sync(recon_ctx *c)
+{
+    if (!c) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!c->launched) return RECON_OK;
+    rk::Ctl h;
+    CK(cudaMemcpy(&h, c->d_ctl, sizeof(h), cudaMemcpyDeviceToHost));
+    c->last_err_tile = (h.err_tile == INT_MAX) ? -1 : h.err_tile;
+    if (h.abort) return RECON_ETIMEOUT;
+    if (c->last_err_tile >= 0) return RECON_EMARKER;
+    return RECON_OK;
+}
+
+extern "C" int recon_last_error_tile(recon_ctx *c)
+{
+    if (!c) return -1;
+    recon_sync(c);
+    return c->last_err_tile;
+}
+
+extern "C" int recon_get_work(recon_ctx *c, recon_work *out, int n)
+{
+    if (!c || !out || n < 0 || n > c->last_n) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n == 0) return RECON_OK;
+    std::vector<rk::Work> w(n);
+    CK(cudaMemcpy(w.data(), c->d_work, sizeof(rk::Work) * n, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) {
+        out[i].visits = w[i].visits;
+        out[i].scan_rows = w[i].scan_rows;
+        out[i].pops = w[i].pops;
+        out[i].seeds = w[i].seeds;
+    }
+    return RECON_OK;
+}
+
+extern "C" int recon_last_kernel_ms(recon_ctx *c, float *ms)
+{
+    if (!c || !ms || !c->launched) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+    return RECON_OK;
+}
+
+// ---------------------------------------------------------------------------
+// end-to-end entry points (host buffers)
+
+extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
+{
+    if (!c || !tiles || n < 1) return RECON_EINVAL;
+    for (int t = 0; t < n; ++t)
+        if (!tile_ok(tiles[t])) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    size_t total = 0;
+    std::vector<size_t> off(n);
+    for (int t = 0; t < n; ++t) {
+        off[t] = total;
+        total += align_up((size_t)tiles[t].H * (size_t)tiles[t].W, 256);
+    }
+    if (c->cap_img < 2 * total) {
+        CK(cudaStreamSynchronize(c->stream));
+        drop_graph(c);
+    }
+    int rc = grow(&c->d_img, &c->cap_img, 2 * total);
+    if (rc) return rc;
+    std::vector<recon_tile> dt(n);
+    for (int t = 0; t < n; ++t) {
+        const recon_tile &T = tiles[t];
+        uint8_t *dI = c->d_img + off[t], *dJ = c->d_img + total + off[t];
+        CK(cudaMemcpy2DAsync(dI, T.W, T.I, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpy2DAsync(dJ, T.W, T.J, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
+        dt[t] = T;
+        dt[t].I = dI; dt[t].J = dJ; dt[t].pitch = T.W;
+    }
+    const unsigned fl = c->flags;
+    c->flags &= ~RECON_FLAG_SYNC;
+    rc = batch_impl(c, dt.data(), n, nullptr, nullptr);
+    c->flags = fl;
+    if (rc) { cudaStreamSynchronize(c->stream); return rc; }
+    for (int t = 0; t < n; ++t) {
+        const recon_tile &T = tiles[t];
+        CK(cudaMemcpy2DAsync(T.J, T.pitch, dt[t].J, T.W, T.W, T.H, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return recon_sync(c);
+}
+
+extern "C" int recon_run_host(recon_ctx *c, const uint8_t *I, uint8_t *J, int H, int W, int conn)
+{
+    recon_tile t;
+    t.I = I; t.J = J; t.H = H; t.W = W; t.pitch = W; t.conn = conn;
+    return recon_batch_host(c, &t, 1);
+}
+
+// ---------------------------------------------------------------------------
+// learned cost model entry points
+
+extern "C" int recon_features(recon_ctx *c, const recon_tile *tiles, int n, float *feat)
+{
+    if (!c || !tiles || n < 1 || !feat) return RECON_EINVAL;
+    for (int t = 0; t < n; ++t)
+        if (!tile_ok(tiles[t])) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<rl_tile> rt(n);
+    for (int t = 0; t < n; ++t) rt[t] = rl_tile{tiles[t].I, tiles[t].J, tiles[t].H, tiles[t].W, tiles[t].pitch};
+    const size_t sb = rl_features_scratch(n), hb = rl_features_stage(n);
+    void *d = nullptr, *h = nullptr;
+    CK(cudaMalloc(&d, sb));
+    cudaError_t e = cudaMallocHost(&h, hb);
+    if (e == cudaSuccess) e = rl_features(rt.data(), n, d, sb, feat, nullptr, 4 * c->sms, c->stream, h, hb);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (h) cudaFreeHost(h);
+    return cuda_status(e);
+}
+
+extern "C" int recon_mlp_forward(recon_ctx *c, const float *theta, const float *X, int n, float *Y)
+{
+    if (!c || !theta || !X || !Y || n < 1) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(rl_forward(theta, X, n, Y, c->stream));
+    if (c->flags & RECON_FLAG_SYNC) CK(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+extern "C" int recon_mlp_grad(recon_ctx *c, const float *theta, const float *X, const float *T, const int *idx,
+                              int n, float *grad, float *loss)
+{
+    if (!c || !theta || !X || !T || !grad || n < 1) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(rl_grad(theta, X, T, idx, n, grad, loss, c->stream));
+    if (c->flags & RECON_FLAG_SYNC) CK(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+extern "C" int recon_mlp_adam(recon_ctx *c, float *theta, float *grad, float *m, float *v, int t, float lr)
+{
+    if (!c || !theta || !grad || !m || !v || t < 1 || !(lr > 0.0f)) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(rl_adam(theta, grad, m, v, t, lr, c->stream));
+    if (c->flags & RECON_FLAG_SYNC) CK(cudaStreamSynchronize(c->stream));
+    return RECON_OK;
+}
+
+static uint64_t sm64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+extern "C" int recon_mlp_train(recon_ctx *c, float *theta, const float *X, const float *T, int n, int epochs,
+                               int batch, float lr, uint64_t seed, float *epoch_loss)
+{
+    if (!c || !theta || !X || !T || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f)) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    float *m = nullptr, *v = nullptr, *g = nullptr, *dl = nullptr;
+    int *didx = nullptr;
+    cudaError_t e = cudaMalloc((void **)&m, sizeof(float) * MLP_NPARAMS * 3);
+    if (e == cudaSuccess) { v = m + MLP_NPARAMS; g = v + MLP_NPARAMS; }
+    if (e == cudaSuccess) e = cudaMemsetAsync(m, 0, sizeof(float) * MLP_NPARAMS * 3, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&didx, sizeof(int) * (size_t)n * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dl, sizeof(float) * epochs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dl, 0, sizeof(float) * epochs, c->stream);
+    std::vector<int> perm(n);
+    int t = 0;
+    const int nbatches = (n + batch - 1) / batch;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+        // Fisher-Yates shuffle driven by SplitMix64 outputs of (seed, epoch)
+        for (int i = 0; i < n; ++i) perm[i] = i;
+        uint64_t st = sm64(seed ^ sm64((uint64_t)ep + 1));
+        for (int i = n - 1; i > 0; --i) {
+            st = sm64(st);
+            const int j = (int)(st % (uint64_t)(i + 1));
+            std::swap(perm[i], perm[j]);
+        }
+        int *buf = didx + (size_t)(ep & 1) * n;  // double-buffered: the copy of epoch e+1 cannot race epoch e
+        e = cudaMemcpyAsync(buf, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // perm is pageable and reused
+        for (int s = 0; s < n && e == cudaSuccess; s += batch) {
+            const int nb = std::min(batch, n - s);
+            e = rl_grad(theta, X, T, buf + s, nb, g, dl + ep, c->stream);
+            if (e == cudaSuccess) e = rl_adam(theta, g, m, v, ++t, lr, c->stream);
+        }
+    }
+    if (e == cudaSuccess && epoch_loss) {
+        e = cudaMemcpyAsync(epoch_loss, dl, sizeof(float) * epochs, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        for (int i = 0; i < epochs; ++i) epoch_loss[i] /= (float)nbatches;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(m);
+    cudaFree(didx);
+    cudaFree(dl);
+    return cuda_status(e);
+}
+
+extern "C" int recon_sched_set_model(recon_ctx *c, const float *theta, const float *norm, int variant_a,
+                                     int variant_b)
+{
+    if (!c) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    const int rc = recon_sched_set(c->sched, theta, norm, variant_a, variant_b);
+    if (rc == RECON_OK) drop_graph(c);
+    return rc;
+}
+
+extern "C" int recon_sched_plan_batch(recon_ctx *c, const recon_tile *tiles, int n, int *variant, int *order,
+                                      float *pred)
+{
+    if (!c || !tiles || n < 1 || !variant || !order) return RECON_EINVAL;
+    for (int t = 0; t < n; ++t)
+        if (!tile_ok(tiles[t])) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    std::vector<int> lv, lo;
+    const int rc = recon_sched_plan(c->sched, tiles, n, c->sms, c->stream, &lv, &lo);
+    if (rc) return rc;
+    std::copy(lv.begin(), lv.end(), variant);
+    std::copy(lo.begin(), lo.end(), order);
+    if (pred) {
+        const std::vector<float> &p = recon_sched_last_pred(c->sched);
+        std::copy(p.begin(), p.begin() + 2 * (size_t)n, pred);
+    }
+    return RECON_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: times candidate (block height, bands, first-visit scan pairs) on
+// the caller's batch and keeps the fastest. Results never differ (R is unique),
+// only the time does.
+
+extern "C" int recon_autotune(recon_ctx *c, const recon_tile *tiles, int n, int reps, int *best)
+{
+    if (!c || !tiles || n < 1 || !best || reps < 1 || reps > 100) return RECON_EINVAL;
+    for (int t = 0; t < n; ++t)
+        if (!tile_ok(tiles[t])) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    // backup of every marker so each trial starts from the same J
+    size_t total = 0;
+    std::vector<size_t> off(n);
+    for (int t = 0; t < n; ++t) {
+        off[t] = total;
+        total += align_up((size_t)tiles[t].H * (size_t)tiles[t].pitch, 256);
+    }
+    uint8_t *bk = nullptr;
+    CK(cudaMalloc((void **)&bk, total));
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < n && e == cudaSuccess; ++t)
+        e = cudaMemcpyAsync(bk + off[t], tiles[t].J, (size_t)tiles[t].H * tiles[t].pitch, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    const int save_bh = c->bh, save_bands = c->bands, save_k = c->k;
+    const unsigned save_flags = c->flags;
+    c->flags &= ~RECON_FLAG_SYNC;
+    float best_ms = 1e30f;
+    int bb[3] = {save_bh, save_bands, save_k};
+    int rc = RECON_OK;
+    const int BHs[3] = {32, 64, 128}, BANDS[3] = {1, 2, 4}, KS[3] = {0, 1, 2};
+    for (int a = 0; a < 3 && e == cudaSuccess && rc == RECON_OK; ++a)
+        for (int b = 0; b < 3 && e == cudaSuccess && rc == RECON_OK; ++b)
+            for (int k = 0; k < 3 && e == cudaSuccess && rc == RECON_OK; ++k) {
+                c->bh = BHs[a]; c->bands = BANDS[b]; c->k = KS[k];
+                drop_graph(c);
+                float sum = 0.0f;
+                for (int r = 0; r < reps + 1 && e == cudaSuccess && rc == RECON_OK; ++r) {
+                    for (int t = 0; t < n && e == cudaSuccess; ++t)
+                        e = cudaMemcpyAsync(tiles[t].J, bk + off[t], (size_t)tiles[t].H * tiles[t].pitch,
+                                            cudaMemcpyDeviceToDevice, c->stream);
+                    if (e != cudaSuccess) break;
+                    rc = batch_impl(c, tiles, n, nullptr, nullptr);
+                    if (rc == RECON_OK) rc = recon_sync(c);
+                    float ms = 0.0f;
+                    if (rc == RECON_OK) e = cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+                    if (r > 0) sum += ms;   // the first run warms up (and builds the graph)
+                }
+                if (rc == RECON_OK && e == cudaSuccess && sum / reps < best_ms) {
+                    best_ms = sum / reps;
+                    bb[0] = BHs[a]; bb[1] = BANDS[b]; bb[2] = KS[k];
+                }
+            }
+    for (int t = 0; t < n && e == cudaSuccess; ++t)
+        e = cudaMemcpyAsync(tiles[t].J, bk + off[t], (size_t)tiles[t].H * tiles[t].pitch, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(bk);
+    c->flags = save_flags;
+    drop_graph(c);
+    if (rc != RECON_OK || e != cudaSuccess) {
+        c->bh = save_bh; c->bands = save_bands; c->k = save_k;
+        return rc != RECON_OK ? rc : cuda_status(e);
+    }
+    c->bh = bb[0]; c->bands = bb[1]; c->k = bb[2];
+    best[0] = bb[0]; best[1] = bb[1]; best[2] = bb[2];
+    return RECON_OK;
+}

@@ -1,0 +1,898 @@
+// Grayscale morphological reconstruction by irregular wavefront propagation
+// (Table II "Morphological Reconstruction"; Sec. III-B Algorithm 1; the hybrid
+// scan-then-queue schedule of Sec. VI-B) for sm_103a.
+//
+// Design. The image is cut into blocks of BH x 128 pixels. One persistent
+// launch pulls blocks from a work list: first every block once, in packing
+// order (the "cold" list), then blocks re-queued because a neighbour raised a
+// pixel on their border (a ring in global memory). A CTA reconstructs its block
+// locally in shared memory against the block's 1-pixel halo:
+//   1. k raster + anti-raster scan pairs (each scan row is one warp: a vertical
+//      max from the previous row, then a warp prefix scan of clamp maps along
+//      the row), or scans until a pair changes nothing (variant k < 0);
+//   2. a seeding pass: one in-place geodesic dilation whose changed pixels form
+//      the frontier (Algorithm 1's initialization phase);
+//   3. the wavefront phase: level-synchronous queue processing in shared
+//      memory (warp-ballot compaction, spill to global memory), each update an
+//      atomic byte max under the mask, J(q) <- max(J(q), min(J(p), I(q))).
+// The block then writes its changed rows and notifies each neighbour block
+// whose halo can now receive a propagation. Every update is a monotone step
+// towards the unique fixed point R, so any order of blocks and updates yields
+// the same bytes. Each block has one writer at a time (the RUN state bit);
+// a notification for a running block sets DIRTY and the runner re-reads its
+// halo before it lets go. Every device-side wait is bounded.
+#include <climits>
+#include <cuda_runtime.h>
+#include "recon_internal.h"
+
+namespace rk {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) { return __vmaxu4(a, b); }
+__device__ __forceinline__ uint32_t vmin(uint32_t a, uint32_t b) { return __vminu4(a, b); }
+// pixel x-1 of each byte lane, taking lane 0's from the previous word's top byte
+__device__ __forceinline__ uint32_t west(uint32_t prev, uint32_t cur) { return __funnelshift_l(prev, cur, 8); }
+// pixel x+1 of each byte lane, taking lane 3's from the next word's low byte
+__device__ __forceinline__ uint32_t east(uint32_t cur, uint32_t next) { return __funnelshift_r(cur, next, 8); }
+
+template <int BH>
+struct Smem {
+    alignas(128) uint32_t J[(BH + 2) * PW];   // TMA destinations: 128-byte aligned
+    alignas(128) uint32_t I[(BH + 2) * PW];   // 0 on the halo: nothing ever propagates into it
+    unsigned long long mbar;                  // TMA completion barrier
+    uint16_t q[2][QCAP];          // BFS levels (byte offsets into J)
+    uint8_t hIt[BW + 2], hIb[BW + 2];  // halo mask, top / bottom rows, x = -1 .. BW
+    uint8_t hIl[BH], hIr[BH];          // halo mask, left / right columns
+    uint8_t eT[BW], eB[BW], eL[BH], eR[BH];  // edge values when neighbours last saw them
+    unsigned rowmask[BH / 32];
+    unsigned cnt[2];              // sizes of the level being filled (two slots, by parity)
+    unsigned item, tile, flag, overflow, notify, visited;
+    unsigned wn, wl;              // hand-back of a warp-only run of small levels
+    unsigned phase;               // parity of the TMA barrier's next completion
+};
+
+__device__ __forceinline__ int find_tile(const Params &P, unsigned b)
+{
+    int lo = 0, hi = P.ntiles - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P.tiles[mid].block_base <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned cold_block(const Params &P, unsigned c)
+{
+    int lo = 0, hi = P.ntiles - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (P.order_base[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return P.tiles[P.order[lo]].block_base + (c - P.order_base[lo]);
+}
+
+__device__ void set_abort(const Params &P) { atomicExch(&P.ctl->abort, 1); }
+
+// Appends block b to the ring of re-queued blocks (the caller already moved
+// its state from IDLE to queued and counted it as outstanding).
+__device__ void push_hot(const Params &P, unsigned b)
+{
+    unsigned long long t = atomicAdd(&P.ctl->tail, 1ull);
+    unsigned *slot = &P.ring[t % P.nblocks];
+    for (int it = 0; atomicCAS(slot, EMPTY, b) != EMPTY; ++it) {
+        if (it > (1 << 22)) { set_abort(P); return; }
+        __nanosleep(64);
+    }
+}
+
+// Marks block a as needing (re)processing because a neighbour changed.
+__device__ void notify_block(const Params &P, unsigned a)
+{
+    unsigned old = *(volatile unsigned *)&P.state[a];
+    unsigned nw;
+    for (;;) {
+        if (old & S_RUN) {
+            if (old & S_DIRTY) return;
+            nw = old | S_DIRTY;
+        } else if (old & S_IDLE) {
+            nw = old & ~S_IDLE;
+        } else {
+            return;  // already queued
+        }
+        unsigned prev = atomicCAS(&P.state[a], old, nw);
+        if (prev == old) break;
+        old = prev;
+    }
+    if (!(old & S_RUN)) {
+        atomicAdd(&P.ctl->outstanding, 1u);
+        push_hot(P, a);
+    }
+}
+
+// Thread 0: next block to process, or EMPTY when all work is done / aborted.
+__device__ unsigned next_item(const Params &P)
+{
+    Ctl *c = P.ctl;
+    unsigned long long idle0 = 0;
+    unsigned sleep = 32;
+    for (;;) {
+        if (*(volatile int *)&c->abort) return EMPTY;
+        unsigned long long h = *(volatile unsigned long long *)&c->head;
+        unsigned long long t = *(volatile unsigned long long *)&c->tail;
+        if (h < t) {
+            if (atomicCAS(&c->head, h, h + 1) == h) {
+                unsigned *slot = &P.ring[h % P.nblocks];
+                unsigned b;
+                for (int it = 0; (b = atomicExch(slot, EMPTY)) == EMPTY; ++it) {
+                    if (it > (1 << 22)) { set_abort(P); return EMPTY; }
+                    __nanosleep(32);
+                }
+                return b;
+            }
+            continue;
+        }
+        if (*(volatile unsigned *)&c->cold < P.nblocks) {
+            unsigned k = atomicAdd(&c->cold, 1u);
+            if (k < P.nblocks) return cold_block(P, k);
+        }
+        if (*(volatile unsigned *)&c->outstanding == 0) return EMPTY;
+        unsigned long long now = gtimer();
+        if (idle0 == 0) idle0 = now;
+        else if ((long long)(now - idle0) > P.wait_ns) { set_abort(P); return EMPTY; }
+        __nanosleep(sleep);
+        if (sleep < 4096) sleep <<= 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// loads
+
+__device__ __forceinline__ uint32_t ld_j_word(const uint8_t *p) { return __ldcg((const unsigned int *)p); }
+__device__ __forceinline__ uint32_t ld_j_byte(const uint8_t *p) { return __ldcg(p); }
+__device__ __forceinline__ uint32_t ld_i_word(const uint8_t *p) { return __ldg((const unsigned int *)p); }
+__device__ __forceinline__ uint32_t ld_i_byte(const uint8_t *p) { return __ldg(p); }
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// TMA: the (BH+2) x 160-byte box of I and of J at (x0 - XOFF, y0 - 1) into
+// shared memory; out-of-image pixels arrive as 0 (the border rule: absent
+// neighbours act as J = 0, the identity of max). One thread issues; every
+// thread waits on the CTA's mbarrier (bounded).
+template <int BH>
+__device__ void tma_load_block(Smem<BH> &S, const Params &P, int t, int y0, int x0)
+{
+    const unsigned bar = smem_addr(&S.mbar);
+    if (threadIdx.x == 0) {
+        const char *tm = (const char *)P.tmaps + (size_t)t * 256;
+        const unsigned long long mI = (unsigned long long)tm, mJ = (unsigned long long)(tm + 128);
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(mI) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(mJ) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const unsigned bytes = 2u * (unsigned)((BH + 2) * BOXW);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+        const int cx = x0 - XOFF, cy = y0 - 1;
+        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                     :: "r"(smem_addr(S.J)), "l"(mJ), "r"(cx), "r"(cy), "r"(bar) : "memory");
+        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                     :: "r"(smem_addr(S.I)), "l"(mI), "r"(cx), "r"(cy), "r"(bar) : "memory");
+    }
+    const unsigned ph = S.phase;
+    unsigned done = 0;
+    for (long it = 0; !done; ++it) {
+        asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
+                     : "=r"(done) : "r"(bar), "r"(ph) : "memory");
+        if (!done && it > (1l << 26)) { set_abort(P); break; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) S.phase = ph ^ 1u;
+    // halo mask out of the box, then zero it in S.I
+    const uint8_t *Ib = (const uint8_t *)S.I;
+    constexpr int RB = PW * 4;
+    for (int x = threadIdx.x - 1; x <= BW; x += NT) {
+        S.hIt[x + 1] = Ib[XOFF + x];
+        S.hIb[x + 1] = Ib[(BH + 1) * RB + XOFF + x];
+    }
+    for (int r = threadIdx.x; r < BH; r += NT) {
+        S.hIl[r] = Ib[(r + 1) * RB + XOFF - 1];
+        S.hIr[r] = Ib[(r + 1) * RB + XOFF + BW];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * (BH + 2) + 2 * PW; i += NT) {
+        if (i < BH + 2) S.I[i * PW + WL] = 0u;
+        else if (i < 2 * (BH + 2)) S.I[(i - (BH + 2)) * PW + WR] = 0u;
+        else if (i < 2 * (BH + 2) + PW) S.I[i - 2 * (BH + 2)] = 0u;
+        else S.I[(BH + 1) * PW + (i - 2 * (BH + 2) - PW)] = 0u;
+    }
+}
+
+// Loads the block (rows y0-1 .. y0+BH, columns x0-1 .. x0+BW) into shared
+// memory with plain loads (any pitch / alignment).
+// halo_only: reload just the J halo ring (the interior is ours and unchanged).
+template <int BH>
+__device__ void load_block(Smem<BH> &S, const TileDesc &D, int y0, int x0, bool halo_only)
+{
+    const int H = D.H, W = D.W;
+    const size_t pitch = (size_t)D.pitch;
+    constexpr int NW = WR - WL + 1;   // 34 words per row: halo, 32 interior, halo
+    for (int idx = threadIdx.x; idx < (BH + 2) * NW; idx += NT) {
+        const int r = idx / NW, w = WL + (idx - r * NW);
+        const bool hrow = (r == 0 || r == BH + 1), hword = (w == WL || w == WR);
+        if (halo_only && !hrow && !hword) continue;
+        const int yy = y0 - 1 + r;
+        uint32_t jv = 0, iv = 0;
+        const bool rowin = (yy >= 0 && yy < H);
+        if (w == WL) {
+            const int x = x0 - 1;
+            if (rowin && x >= 0) {
+                jv = ld_j_byte(D.J + yy * pitch + x) << 24;
+                if (!halo_only) iv = ld_i_byte(D.I + yy * pitch + x) << 24;
+            }
+        } else if (w == WR) {
+            const int x = x0 + BW;
+            if (rowin && x < W) {
+                jv = ld_j_byte(D.J + yy * pitch + x);
+                if (!halo_only) iv = ld_i_byte(D.I + yy * pitch + x);
+            }
+        } else if (rowin) {
+            const int x = x0 + 4 * (w - W0);
+            if (D.fast && x + 3 < W) {
+                jv = ld_j_word(D.J + yy * pitch + x);
+                if (!halo_only) iv = ld_i_word(D.I + yy * pitch + x);
+            } else {
+                for (int b = 0; b < 4; ++b)
+                    if (x + b < W) {
+                        jv |= ld_j_byte(D.J + yy * pitch + x + b) << (8 * b);
+                        if (!halo_only) iv |= ld_i_byte(D.I + yy * pitch + x + b) << (8 * b);
+                    }
+            }
+        }
+        S.J[r * PW + w] = jv;
+        if (halo_only) continue;
+        S.I[r * PW + w] = (hrow || hword) ? 0u : iv;
+        if (hrow) {
+            uint8_t *h = (r == 0) ? S.hIt : S.hIb;
+            if (w == WL) h[0] = (uint8_t)(iv >> 24);
+            else if (w == WR) h[BW + 1] = (uint8_t)iv;
+            else for (int b = 0; b < 4; ++b) h[4 * (w - W0) + b + 1] = (uint8_t)(iv >> (8 * b));
+        } else if (w == WL) {
+            S.hIl[r - 1] = (uint8_t)(iv >> 24);
+        } else if (w == WR) {
+            S.hIr[r - 1] = (uint8_t)iv;
+        }
+    }
+}
+
+template <int BH>
+__device__ __forceinline__ uint8_t jbyte(const Smem<BH> &S, int r, int x)  // x in -1 .. BW
+{
+    return ((const volatile uint8_t *)S.J)[r * PW * 4 + XOFF + x];
+}
+
+template <int BH>
+__device__ void save_edges(Smem<BH> &S)
+{
+    for (int i = threadIdx.x; i < BW; i += NT) {
+        S.eT[i] = jbyte(S, 1, i);
+        S.eB[i] = jbyte(S, BH, i);
+    }
+    for (int i = threadIdx.x; i < BH; i += NT) {
+        S.eL[i] = jbyte(S, i + 1, 0);
+        S.eR[i] = jbyte(S, i + 1, BW - 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// scans: one warp over rows [r0, r1) of the block (shared-memory row indices)
+
+__device__ __forceinline__ uint32_t map_pack(uint32_t A, uint32_t C) { return A | (C << 8); }
+
+// composition g o f of clamp maps v -> min(C, max(A, v)); g = (A, C) applied after f = (fA, fC)
+__device__ __forceinline__ uint32_t compose(uint32_t g, uint32_t f)
+{
+    const uint32_t A = g & 0xFF, C = g >> 8, fA = f & 0xFF, fC = f >> 8;
+    return map_pack(min(C, max(A, fA)), min(C, max(A, fC)));
+}
+
+template <int BH, int CONN>
+__device__ bool raster_rows(Smem<BH> &S, int r0, int r1)
+{
+    const int lane = threadIdx.x & 31, w = lane + W0;
+    bool any = false;
+    for (int y = r0; y < r1; ++y) {
+        __syncwarp();
+        const uint32_t *up = &S.J[(y - 1) * PW];
+        const uint32_t u = up[w];
+        uint32_t vert = u;
+        if (CONN == 8) vert = vmax(vert, vmax(west(up[w - 1], u), east(u, up[w + 1])));
+        const uint32_t j = S.J[y * PW + w], i = S.I[y * PW + w];
+        const uint32_t a = vmin(i, vmax(j, vert));
+        // per-byte clamp maps (a, i), composed left to right inside the word
+        const uint32_t A1 = vmin(i, vmax(a, a << 8));
+        const uint32_t C1 = vmin(i, vmax(a, (i << 8) | 0xFFu));
+        const uint32_t A2 = vmin(C1, vmax(A1, A1 << 16));
+        const uint32_t C2 = vmin(C1, vmax(A1, (C1 << 16) | 0xFFFFu));
+        uint32_t m = map_pack(A2 >> 24, C2 >> 24);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(FULL, m, d);
+            if (lane >= d) m = compose(m, o);
+        }
+        uint32_t ex = __shfl_up_sync(FULL, m, 1);
+        if (lane == 0) ex = map_pack(0, 255);
+        const uint32_t h = S.J[y * PW + WL] >> 24;  // pixel x = -1 of this row (halo)
+        const uint32_t vin = min(ex >> 8, max(ex & 0xFF, h));
+        const uint32_t r = vmin(C2, vmax(A2, vin * 0x01010101u));
+        const bool ch = (r != j);
+        if (ch) S.J[y * PW + w] = r;
+        if (__any_sync(FULL, ch)) {
+            any = true;
+            if (lane == 0) atomicOr(&S.rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
+        }
+    }
+    return any;
+}
+
+template <int BH, int CONN>
+__device__ bool antiraster_rows(Smem<BH> &S, int r0, int r1)
+{
+    const int lane = threadIdx.x & 31, w = lane + W0;
+    bool any = false;
+    for (int y = r1 - 1; y >= r0; --y) {
+        __syncwarp();
+        const uint32_t *dn = &S.J[(y + 1) * PW];
+        const uint32_t d = dn[w];
+        uint32_t vert = d;
+        if (CONN == 8) vert = vmax(vert, vmax(west(dn[w - 1], d), east(d, dn[w + 1])));
+        const uint32_t j = S.J[y * PW + w], i = S.I[y * PW + w];
+        const uint32_t a = vmin(i, vmax(j, vert));
+        // composed right to left inside the word
+        const uint32_t A1 = vmin(i, vmax(a, a >> 8));
+        const uint32_t C1 = vmin(i, vmax(a, (i >> 8) | 0xFF000000u));
+        const uint32_t A2 = vmin(C1, vmax(A1, A1 >> 16));
+        const uint32_t C2 = vmin(C1, vmax(A1, (C1 >> 16) | 0xFFFF0000u));
+        uint32_t m = map_pack(A2 & 0xFF, C2 & 0xFF);
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const uint32_t o = __shfl_down_sync(FULL, m, s);
+            if (lane + s < 32) m = compose(m, o);
+        }
+        uint32_t ex = __shfl_down_sync(FULL, m, 1);
+        if (lane == 31) ex = map_pack(0, 255);
+        const uint32_t h = S.J[y * PW + WR] & 0xFF;  // pixel x = BW of this row (halo)
+        const uint32_t vin = min(ex >> 8, max(ex & 0xFF, h));
+        const uint32_t r = vmin(C2, vmax(A2, vin * 0x01010101u));
+        const bool ch = (r != j);
+        if (ch) S.J[y * PW + w] = r;
+        if (__any_sync(FULL, ch)) {
+            any = true;
+            if (lane == 0) atomicOr(&S.rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
+        }
+    }
+    return any;
+}
+
+// One raster + anti-raster pair over the whole block; `bands` warps each take a
+// horizontal band of rows. Returns (block-uniformly) whether any pixel changed.
+template <int BH, int CONN>
+__device__ bool scan_pair(Smem<BH> &S, int bands, unsigned long long &rows)
+{
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) S.flag = 0;
+    __syncthreads();
+    bool ch = false;
+    if (warp < bands) {
+        const int r0 = 1 + warp * BH / bands, r1 = 1 + (warp + 1) * BH / bands;
+        ch = raster_rows<BH, CONN>(S, r0, r1);
+        ch |= antiraster_rows<BH, CONN>(S, r0, r1);
+    }
+    if (ch && (threadIdx.x & 31) == 0) S.flag = 1;
+    rows += 2 * BH;
+    __syncthreads();
+    const bool any = S.flag != 0;
+    __syncthreads();  // everyone has read the flag before it is reset again
+    return any;
+}
+
+// ---------------------------------------------------------------------------
+// queue phase
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <int BH>
+__device__ __forceinline__ void put_entry(Smem<BH> &S, uint16_t *gsp, int lvl, unsigned slot, uint16_t v)
+{
+    if (slot < (unsigned)QCAP) S.q[lvl][slot] = v;
+    else if (slot - QCAP < (unsigned)GCAP) gsp[lvl * GCAP + (slot - QCAP)] = v;
+    else S.overflow = 1;
+}
+
+template <int BH>
+__device__ __forceinline__ uint16_t get_entry(const Smem<BH> &S, const uint16_t *gsp, int lvl, unsigned i)
+{
+    return i < (unsigned)QCAP ? S.q[lvl][i] : gsp[lvl * GCAP + (i - QCAP)];
+}
+
+// warp-aggregated append of pixel offset v (when pred) to level lvl
+template <int BH>
+__device__ __forceinline__ void warp_push(Smem<BH> &S, uint16_t *gsp, int lvl, bool pred, uint16_t v)
+{
+    const unsigned bal = __ballot_sync(FULL, pred);
+    if (!bal) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&S.cnt[lvl], (unsigned)__popc(bal));
+    base = __shfl_sync(FULL, base, leader);
+    if (pred) put_entry(S, gsp, lvl, base + __popc(bal & lanemask_lt()), v);
+}
+
+// Seeding pass: J(p) <- max(J(p), min(I(p), max over N(p) of J)) in place;
+// every raised pixel joins level 0. Returns the level's size.
+template <int BH, int CONN>
+__device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp)
+{
+    if (threadIdx.x == 0) { S.cnt[0] = 0; S.overflow = 0; }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = lane + W0;
+    for (int y = 1 + (threadIdx.x >> 5); y <= BH; y += NT / 32) {
+        const uint32_t *rw = &S.J[y * PW];
+        const uint32_t c = rw[w];
+        uint32_t m = vmax(c, vmax(west(rw[w - 1], c), east(c, rw[w + 1])));
+        const uint32_t *up = rw - PW, *dn = rw + PW;
+        const uint32_t u = up[w], d = dn[w];
+        m = vmax(m, vmax(u, d));
+        if (CONN == 8) {
+            m = vmax(m, vmax(west(up[w - 1], u), east(u, up[w + 1])));
+            m = vmax(m, vmax(west(dn[w - 1], d), east(d, dn[w + 1])));
+        }
+        const uint32_t nv = vmin(S.I[y * PW + w], m);
+        const uint32_t diff = nv ^ c;
+        if (diff) S.J[y * PW + w] = nv;
+        if (__any_sync(FULL, diff != 0) && lane == 0)
+            atomicOr(&S.rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            warp_push(S, gsp, 0, ((diff >> (8 * b)) & 0xFFu) != 0, (uint16_t)((y * PW + w) * 4 + b));
+    }
+    __syncthreads();
+    return S.cnt[0];
+}
+
+// byte-wise atomic max on the shared J: returns true if it raised the byte
+__device__ __forceinline__ bool atomic_max_u8(uint32_t *Jw, unsigned off, uint32_t v);
+
+// Seeding of a block that was already at its fixed point for its previous
+// halo (a revisit): its interior is unchanged since, so only the pixels next to
+// the halo (the block's 1-pixel frame) can be raised. Each frame pixel takes
+// one geodesic dilation step; the raised ones form level 0.
+template <int BH, int CONN>
+__device__ unsigned seed_frame(Smem<BH> &S, uint16_t *gsp)
+{
+    constexpr int RB = PW * 4;
+    constexpr int NFR = 2 * BW + 2 * (BH - 2);
+    if (threadIdx.x == 0) { S.cnt[0] = 0; S.overflow = 0; }
+    __syncthreads();
+    const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
+    const uint8_t *Ib = (const uint8_t *)S.I;
+    for (int base = 0; base < NFR; base += NT) {
+        const int i = base + threadIdx.x;
+        const bool act = i < NFR;
+        int r = 1, x = 0;
+        if (i < BW) { r = 1; x = i; }
+        else if (i < 2 * BW) { r = BH; x = i - BW; }
+        else if (i < 2 * BW + (BH - 2)) { r = 2 + (i - 2 * BW); x = 0; }
+        else { r = 2 + (i - 2 * BW - (BH - 2)); x = BW - 1; }
+        const unsigned p = (unsigned)(r * RB + XOFF + x);
+        bool raised = false;
+        if (act) {
+            uint32_t m = Jb[p - RB];
+            m = max(m, (uint32_t)Jb[p + RB]);
+            m = max(m, (uint32_t)Jb[p - 1]);
+            m = max(m, (uint32_t)Jb[p + 1]);
+            if (CONN == 8) {
+                m = max(m, (uint32_t)Jb[p - RB - 1]);
+                m = max(m, (uint32_t)Jb[p - RB + 1]);
+                m = max(m, (uint32_t)Jb[p + RB - 1]);
+                m = max(m, (uint32_t)Jb[p + RB + 1]);
+            }
+            const uint32_t nv = min(m, (uint32_t)Ib[p]);
+            if (nv > Jb[p] && atomic_max_u8(S.J, p, nv)) {
+                raised = true;
+                atomicOr(&S.rowmask[(r - 1) >> 5], 1u << ((r - 1) & 31));
+            }
+        }
+        warp_push(S, gsp, 0, raised, (uint16_t)p);
+    }
+    __syncthreads();
+    return S.cnt[0];
+}
+
+
+__device__ __forceinline__ bool atomic_max_u8(uint32_t *Jw, unsigned off, uint32_t v)
+{
+    uint32_t *wp = Jw + (off >> 2);
+    const unsigned sh = (off & 3) * 8;
+    uint32_t old = *(volatile uint32_t *)wp;
+    for (;;) {
+        if (((old >> sh) & 0xFFu) >= v) return false;
+        const uint32_t nw = (old & ~(0xFFu << sh)) | (v << sh);
+        const uint32_t prev = atomicCAS(wp, old, nw);
+        if (prev == old) return true;
+        old = prev;
+    }
+}
+
+// Processes the wavefront level by level until it is empty (Algorithm 1's
+// propagation phase). n0 = size of level 0. Returns entries processed.
+template <int BH, int CONN>
+__device__ unsigned long long run_queue(Smem<BH> &S, uint16_t *gsp, unsigned n0)
+{
+    constexpr int RB = PW * 4;  // bytes per shared row
+    const int offs8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
+    const int offs4[4] = {-RB, -1, 1, RB};
+    const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
+    const uint8_t *Ib = (const uint8_t *)S.I;
+    unsigned long long pops = 0;
+    unsigned n = n0;
+    int lvl = 0;
+    while (n > 0) {
+        if (n <= 32) {
+            // Small levels (thin fronts): warp 0 alone runs them with warp-level
+            // synchronisation only, until a level grows past 64 entries or the
+            // front dies out; then all warps take over again.
+            if ((threadIdx.x >> 5) == 0) {
+                const int lane = threadIdx.x & 31;
+                unsigned nn = n;
+                int l = lvl;
+                while (nn > 0 && nn <= 64) {
+                    pops += nn;
+                    unsigned total = 0;
+                    for (unsigned base = 0; base < nn; base += 32) {
+                        const unsigned i = base + lane;
+                        const bool act = i < nn;
+                        const unsigned p = act ? (unsigned)S.q[l][i] : 0u;
+                        const uint32_t v = act ? Jb[p] : 0u;
+#pragma unroll
+                        for (int k = 0; k < CONN; ++k) {
+                            const unsigned q = p + (CONN == 8 ? offs8[k] : offs4[k]);
+                            bool raised = false;
+                            if (act) {
+                                const uint32_t c = min(v, (uint32_t)Ib[q]);
+                                if (Jb[q] < c && atomic_max_u8(S.J, q, c)) {
+                                    raised = true;
+                                    const unsigned row = q / RB;
+                                    atomicOr(&S.rowmask[(row - 1) >> 5], 1u << ((row - 1) & 31));
+                                }
+                            }
+                            const unsigned bal = __ballot_sync(FULL, raised);
+                            if (raised) S.q[l ^ 1][total + __popc(bal & lanemask_lt())] = (uint16_t)q;
+                            total += __popc(bal);
+                        }
+                    }
+                    __syncwarp();
+                    nn = total;
+                    l ^= 1;
+                }
+                if (lane == 0) { S.wn = nn; S.wl = (unsigned)l; }
+            }
+            __syncthreads();
+            n = S.wn;
+            lvl = (int)S.wl;
+            __syncthreads();
+            continue;
+        }
+        const unsigned navail = min(n, (unsigned)(QCAP + GCAP));
+        pops += navail;
+        // the slot being reset was last read before the previous barrier
+        if (threadIdx.x == 0) S.cnt[lvl ^ 1] = 0;
+        __syncthreads();
+        for (unsigned base = 0; base < navail; base += NT) {
+            const unsigned i = base + threadIdx.x;
+            const bool act = i < navail;
+            const unsigned p = act ? get_entry(S, gsp, lvl, i) : 0u;
+            const uint32_t v = act ? Jb[p] : 0u;
+#pragma unroll
+            for (int k = 0; k < CONN; ++k) {
+                const unsigned q = p + (CONN == 8 ? offs8[k] : offs4[k]);
+                bool raised = false;
+                if (act) {
+                    const uint32_t c = min(v, (uint32_t)Ib[q]);
+                    if (Jb[q] < c && atomic_max_u8(S.J, q, c)) {
+                        raised = true;
+                        const unsigned row = q / RB;
+                        atomicOr(&S.rowmask[(row - 1) >> 5], 1u << ((row - 1) & 31));
+                    }
+                }
+                warp_push(S, gsp, lvl ^ 1, raised, (uint16_t)q);
+            }
+        }
+        __syncthreads();
+        n = S.cnt[lvl ^ 1];
+        lvl ^= 1;
+    }
+    return pops;
+}
+
+// ---------------------------------------------------------------------------
+
+template <int BH>
+__device__ void write_back(Smem<BH> &S, const TileDesc &D, int y0, int x0)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t pitch = (size_t)D.pitch;
+    for (int r = warp; r < BH; r += NT / 32) {
+        if (!((S.rowmask[r >> 5] >> (r & 31)) & 1u)) continue;
+        const int yy = y0 + r;
+        if (yy >= D.H) break;
+        const int x = x0 + 4 * lane;
+        const uint32_t v = S.J[(r + 1) * PW + lane + W0];
+        uint8_t *dst = D.J + yy * pitch + x;
+        if (D.fast && x + 3 < D.W) {
+            *(uint32_t *)dst = v;
+        } else {
+            for (int b = 0; b < 4; ++b)
+                if (x + b < D.W) dst[b] = (uint8_t)(v >> (8 * b));
+        }
+    }
+}
+
+// direction bits for neighbour notification
+enum { DN = 1, DS = 2, DW = 4, DE = 8, DNW = 16, DNE = 32, DSW = 64, DSE = 128 };
+
+template <int BH, int CONN>
+__device__ void edge_notify_bits(Smem<BH> &S)
+{
+    unsigned bits = 0;
+    for (int x = threadIdx.x; x < BW; x += NT) {
+        const uint32_t vt = jbyte(S, 1, x), vb = jbyte(S, BH, x);
+        for (int dx = (CONN == 8 ? -1 : 0); dx <= (CONN == 8 ? 1 : 0); ++dx) {
+            const int qx = x + dx;
+            const unsigned dirN = qx < 0 ? DNW : (qx >= BW ? DNE : DN);
+            const unsigned dirS = qx < 0 ? DSW : (qx >= BW ? DSE : DS);
+            if (vt != S.eT[x] && jbyte(S, 0, qx) < min(vt, (uint32_t)S.hIt[qx + 1])) bits |= dirN;
+            if (vb != S.eB[x] && jbyte(S, BH + 1, qx) < min(vb, (uint32_t)S.hIb[qx + 1])) bits |= dirS;
+        }
+    }
+    for (int r = 1 + threadIdx.x; r <= BH; r += NT) {
+        const uint32_t vl = jbyte(S, r, 0), vr = jbyte(S, r, BW - 1);
+        for (int dy = (CONN == 8 ? -1 : 0); dy <= (CONN == 8 ? 1 : 0); ++dy) {
+            const int qr = r + dy;
+            const uint32_t il = qr == 0 ? S.hIt[0] : (qr == BH + 1 ? S.hIb[0] : S.hIl[qr - 1]);
+            const uint32_t ir = qr == 0 ? S.hIt[BW + 1] : (qr == BH + 1 ? S.hIb[BW + 1] : S.hIr[qr - 1]);
+            const unsigned dirW = qr == 0 ? DNW : (qr == BH + 1 ? DSW : DW);
+            const unsigned dirE = qr == 0 ? DNE : (qr == BH + 1 ? DSE : DE);
+            if (vl != S.eL[r - 1] && jbyte(S, qr, -1) < min(vl, il)) bits |= dirW;
+            if (vr != S.eR[r - 1] && jbyte(S, qr, BW) < min(vr, ir)) bits |= dirE;
+        }
+    }
+    if (bits) atomicOr(&S.notify, bits);
+}
+
+// Returns true when the block's state was released here (normal path), false
+// when the caller must release it (tile failed the marker check).
+template <int BH, int CONN>
+__device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, unsigned b,
+                              int t, uint16_t *gsp, Work &wk)
+{
+    const unsigned local = b - D.block_base;
+    const int by = (int)(local / (unsigned)D.nbx), bx = (int)(local % (unsigned)D.nbx);
+    const int y0 = by * BH, x0 = bx * BW;
+    const bool visited = S.visited != 0;
+
+    for (int i = threadIdx.x; i < BH / 32; i += NT) S.rowmask[i] = 0;
+    if (threadIdx.x == 0) { S.notify = 0; S.flag = 0; }
+    if (D.fast == 2) tma_load_block(S, P, t, y0, x0);
+    else load_block(S, D, y0, x0, false);
+    __syncthreads();
+
+    if (!visited && P.check) {
+        bool bad = false;
+        for (int idx = threadIdx.x; idx < BH * WPR; idx += NT) {
+            const int o = (1 + idx / WPR) * PW + W0 + idx % WPR;
+            if (__vcmpgtu4(S.J[o], S.I[o])) bad = true;
+        }
+        if (bad) S.flag = 1;
+        __syncthreads();
+        if (S.flag) {
+            if (threadIdx.x == 0) {
+                atomicExch(&P.tile_err[t], 2);
+                atomicMin(&P.ctl->err_tile, t);
+            }
+            return false;
+        }
+    }
+    save_edges(S);
+    __syncthreads();
+
+    const int k = D.k;
+    bool need_seed = true;
+    // a visited block sits at its fixed point for the halo it last saw
+    bool frame_only = visited;
+    if (!visited || k < 0) {
+        const int pairs = k < 0 ? INT_MAX : k;
+        for (int s = 0; s < pairs; ++s) {
+            if (!scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) { if (k < 0) need_seed = false; break; }
+        }
+    }
+    for (;;) {
+        if (need_seed) {
+            unsigned n = frame_only ? seed_frame<BH, CONN>(S, gsp) : seed_pass<BH, CONN>(S, gsp);
+            wk.seeds += 1;
+            wk.pops += run_queue<BH, CONN>(S, gsp, n);
+            while (S.overflow) {  // a level overflowed: rediscover the frontier
+                __syncthreads();
+                n = seed_pass<BH, CONN>(S, gsp);
+                wk.seeds += 1;
+                wk.pops += run_queue<BH, CONN>(S, gsp, n);
+            }
+        }
+        __syncthreads();
+        write_back(S, D, y0, x0);
+        __threadfence();
+        edge_notify_bits<BH, CONN>(S);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned bits = S.notify;
+            const int dys[8] = {-1, 1, 0, 0, -1, -1, 1, 1}, dxs[8] = {0, 0, -1, 1, -1, 1, -1, 1};
+            for (int d = 0; d < 8; ++d)
+                if (bits & (1u << d)) {
+                    const int ny = by + dys[d], nx = bx + dxs[d];
+                    if (ny >= 0 && ny < D.nby && nx >= 0 && nx < D.nbx)
+                        notify_block(P, D.block_base + (unsigned)(ny * D.nbx + nx));
+                }
+            // let go of the block unless a neighbour changed our halo meanwhile
+            const unsigned prev = atomicCAS(&P.state[b], S_RUN | S_VIS, S_IDLE | S_VIS);
+            S.flag = (prev == (S_RUN | S_VIS)) ? 0u : 1u;
+            if (S.flag) atomicAnd(&P.state[b], ~S_DIRTY);
+            S.notify = 0;
+        }
+        save_edges(S);
+        for (int i = threadIdx.x; i < BH / 32; i += NT) S.rowmask[i] = 0;
+        __syncthreads();
+        if (!S.flag) return true;
+        __threadfence();
+        load_block(S, D, y0, x0, true);  // fresh halo, then converge again
+        wk.visits += 1;
+        __syncthreads();
+        if (k < 0) {
+            need_seed = false;
+            while (scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) {}
+        } else {
+            need_seed = true;
+            frame_only = true;
+        }
+    }
+}
+
+template <int BH>
+__global__ void __launch_bounds__(NT) recon_persistent(Params P)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem<BH> &S = *reinterpret_cast<Smem<BH> *>(smem_raw);
+    uint16_t *gsp = P.spill + (size_t)blockIdx.x * 2 * GCAP;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.phase = 0;
+    }
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned b = next_item(P);
+            S.item = b;
+            if (b != EMPTY) {
+                const int t = find_tile(P, b);
+                S.tile = (unsigned)t;
+                const unsigned old = atomicOr(&P.state[b], S_RUN | S_VIS);
+                S.visited = (old & S_VIS) ? 1u : 0u;
+            }
+        }
+        __syncthreads();
+        const unsigned b = S.item;
+        if (b == EMPTY) return;
+        const int t = (int)S.tile;
+        const TileDesc D = P.tiles[t];
+        Work wk = {1, 0, 0, 0};
+        bool released = false;
+        if (*(volatile int *)&P.tile_err[t] == 0) {
+            if (D.conn == 8) released = process_block<BH, 8>(S, P, D, b, t, gsp, wk);
+            else released = process_block<BH, 4>(S, P, D, b, t, gsp, wk);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // failed tile: drop the block without touching its pixels
+            if (!released) atomicExch(&P.state[b], S_IDLE | S_VIS);
+            atomicAdd(&P.work[t].visits, wk.visits);
+            atomicAdd(&P.work[t].scan_rows, wk.scan_rows);
+            atomicAdd(&P.work[t].pops, wk.pops);
+            atomicAdd(&P.work[t].seeds, wk.seeds);
+            __threadfence();
+            atomicSub(&P.ctl->outstanding, 1u);
+        }
+    }
+}
+
+__global__ void recon_init_kernel(Params P)
+{
+    const size_t n = P.nblocks;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        P.state[i] = 0u;
+        P.ring[i] = EMPTY;
+    }
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)P.ntiles;
+         i += (size_t)gridDim.x * blockDim.x) {
+        P.tile_err[i] = 0;
+        P.work[i] = Work{0, 0, 0, 0};
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.ctl->head = 0;
+        P.ctl->tail = 0;
+        P.ctl->outstanding = P.nblocks + (P.phantom ? 1u : 0u);
+        P.ctl->cold = 0;
+        P.ctl->abort = 0;
+        P.ctl->err_tile = INT_MAX;
+    }
+}
+
+}  // namespace rk
+
+// ---------------------------------------------------------------------------
+// launch helpers used by the host API
+
+extern "C" size_t rk_smem_bytes(int bh)
+{
+    switch (bh) {
+    case 32: return sizeof(rk::Smem<32>);
+    case 64: return sizeof(rk::Smem<64>);
+    case 128: return sizeof(rk::Smem<128>);
+    }
+    return 0;
+}
+
+extern "C" cudaError_t rk_configure(int bh, int *ctas_per_sm)
+{
+    const void *fn = nullptr;
+    switch (bh) {
+    case 32: fn = (const void *)rk::recon_persistent<32>; break;
+    case 64: fn = (const void *)rk::recon_persistent<64>; break;
+    case 128: fn = (const void *)rk::recon_persistent<128>; break;
+    default: return cudaErrorInvalidValue;
+    }
+    const size_t sm = rk_smem_bytes(bh);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, rk::NT, sm);
+}
+
+extern "C" cudaError_t rk_launch_init(int grid, const rk::Params *P, cudaStream_t st)
+{
+    rk::recon_init_kernel<<<grid, 256, 0, st>>>(*P);
+    return cudaGetLastError();
+}
+
+extern "C" cudaError_t rk_launch_main(int bh, int grid, const rk::Params *P, cudaStream_t st)
+{
+    const size_t sm = rk_smem_bytes(bh);
+    switch (bh) {
+    case 32: rk::recon_persistent<32><<<grid, rk::NT, sm, st>>>(*P); break;
+    case 64: rk::recon_persistent<64><<<grid, rk::NT, sm, st>>>(*P); break;
+    case 128: rk::recon_persistent<128><<<grid, rk::NT, sm, st>>>(*P); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
