@@ -112,8 +112,13 @@ enum {
     RECON_P_ORDER = 6,       /* default packing order: 0 = as given, 1 = largest area first */
     RECON_P_TEST_STALL = 7,  /* testing: 1 = add a phantom unit of work that never ends,
                                 so the bounded wait must run out (RECON_ETIMEOUT) */
-    RECON_P_TMA = 8          /* 1 (default): tiles whose rows and bases are 16-byte aligned
+    RECON_P_TMA = 8,         /* 1 (default): tiles whose rows and bases are 16-byte aligned
                                 are loaded into shared memory by TMA; 0 = plain loads */
+    RECON_P_TRACE = 9,       /* diagnostics: 1 = kernels record per-warp progress in mapped
+                                host memory (read with recon_trace, even while running) */
+    RECON_P_LAST_ABORT = 10  /* read-only: which device-side bound ran out in the last call
+                                (0 = none; 1 rerun, 2 overflow, 3 levels, 4 scans, 5 CAS,
+                                6 notify, 7 ring slot, 8 idle wait, 9 ring push, 10 TMA) */
 };
 int recon_set_param(recon_ctx *ctx, int key, int64_t value);
 int64_t recon_get_param(recon_ctx *ctx, int key);
@@ -126,6 +131,15 @@ typedef struct {
     uint64_t pops;        /* queue entries processed */
     uint64_t seeds;       /* seeding passes over a block */
 } recon_work;
+
+/* Waits at most timeout_ms for the context's stream: the device status as
+ * recon_sync when it finished in time, RECON_ETIMEOUT (nothing changed) if not. */
+int recon_sync_for(recon_ctx *ctx, int timeout_ms);
+
+/* Diagnostics (RECON_P_TRACE = 1): copies up to n progress words of the last
+ * launch, one per warp: (code << 24) | block index. Readable while a kernel is
+ * still running. Returns the number of words copied. */
+int recon_trace(recon_ctx *ctx, unsigned *out, int n);
 
 /* Copies the counters of the last call's first n tiles into out[] (syncs). */
 int recon_get_work(recon_ctx *ctx, recon_work *out, int n);

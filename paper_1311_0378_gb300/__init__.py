@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "librecon.so")
 RECON_OK, RECON_EINVAL, RECON_EMARKER, RECON_ENOMEM, RECON_ECUDA, RECON_ETIMEOUT = range(6)
 RECON_FLAG_SYNC, RECON_FLAG_NO_CHECK, RECON_FLAG_LEARNED, RECON_FLAG_NO_GRAPH = 1, 2, 4, 8
 (RECON_P_BLOCK_H, RECON_P_SWEEPS, RECON_P_GRID, RECON_P_BANDS, RECON_P_WAIT_NS, RECON_P_ORDER,
- RECON_P_TEST_STALL, RECON_P_TMA) = range(1, 9)
+ RECON_P_TEST_STALL, RECON_P_TMA, RECON_P_TRACE, RECON_P_LAST_ABORT) = range(1, 11)
 
 # every symbol the header declares; tests check the library exports them all
 SYMBOLS = ("recon_init", "recon_run", "recon_batch", "recon_batch_ex", "recon_run_host",
@@ -28,7 +28,7 @@ SYMBOLS = ("recon_init", "recon_run", "recon_batch", "recon_batch_ex", "recon_ru
            "recon_strerror", "recon_set_param", "recon_get_param", "recon_get_work",
            "recon_last_kernel_ms", "recon_features", "recon_mlp_forward", "recon_mlp_grad",
            "recon_mlp_adam", "recon_mlp_train", "recon_sched_set_model", "recon_sched_plan_batch",
-           "recon_autotune")
+           "recon_autotune", "recon_sync_for", "recon_trace")
 RECON_NFEAT, RECON_MLP_NPARAMS = 20, 5634
 
 
@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
         "recon_sched_set_model": ([vp, vp, vp, i, i], i),
         "recon_sched_plan_batch": ([vp, tp, i, vp, vp, vp], i),
         "recon_autotune": ([vp, tp, i, i, vp], i),
+        "recon_sync_for": ([vp, i], i),
+        "recon_trace": ([vp, vp, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -234,3 +236,13 @@ def recon_autotune(ctx, tiles, reps: int = 2):
     best = (ctypes.c_int * 3)()
     rc = lib().recon_autotune(ctx, _tiles(tiles), len(tiles), reps, best)
     return rc, tuple(best)
+
+
+def recon_sync_for(ctx, timeout_ms: int) -> int:
+    return lib().recon_sync_for(ctx, timeout_ms)
+
+
+def recon_trace(ctx, n: int):
+    out = (ctypes.c_uint * max(n, 1))()
+    m = lib().recon_trace(ctx, out, n)
+    return list(out[:max(m, 0)])

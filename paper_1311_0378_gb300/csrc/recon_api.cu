@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 #include <algorithm>
+#include <time.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -44,6 +45,9 @@ struct recon_ctx {
     int last_n = 0;
     int launched = 0;
     int last_err_tile = -1;
+    int last_abort = 0;
+    // diagnostics: per-warp progress words in mapped host memory
+    unsigned *h_trace = nullptr; unsigned *d_trace = nullptr; size_t cap_trace = 0; int trace_on = 0;
     // graph cache
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gsig;
@@ -134,6 +138,7 @@ extern "C" int recon_free(recon_ctx *c)
     cudaFree(c->d_spill);
     cudaFree(c->d_img);
     if (c->h_meta) cudaFreeHost(c->h_meta);
+    if (c->h_trace) cudaFreeHost(c->h_trace);
     if (c->meta_free) cudaEventDestroy(c->meta_free);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -192,6 +197,9 @@ extern "C" int recon_set_param(recon_ctx *c, int key, int64_t v)
     case RECON_P_TMA:
         if (v != 0 && v != 1) return RECON_EINVAL;
         c->use_tma = (int)v; break;
+    case RECON_P_TRACE:
+        if (v != 0 && v != 1) return RECON_EINVAL;
+        c->trace_on = (int)v; break;
     default: return RECON_EINVAL;
     }
     drop_graph(c);
@@ -215,6 +223,8 @@ extern "C" int64_t recon_get_param(recon_ctx *c, int key)
     case RECON_P_ORDER: return c->order_policy;
     case RECON_P_TEST_STALL: return c->phantom;
     case RECON_P_TMA: return c->use_tma;
+    case RECON_P_TRACE: return c->trace_on;
+    case RECON_P_LAST_ABORT: return c->last_abort;
     }
     return -1;
 }
@@ -415,6 +425,22 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
     P.bands = c->bands;
     P.phantom = c->phantom;
     P.check = (c->flags & RECON_FLAG_NO_CHECK) ? 0 : 1;
+    P.trace = nullptr;
+    if (c->trace_on) {
+        const size_t words = (size_t)grid * (rk::NT / 32);
+        if (c->cap_trace < words) {
+            CK(cudaStreamSynchronize(c->stream));
+            drop_graph(c);
+            if (c->h_trace) cudaFreeHost(c->h_trace);
+            c->h_trace = nullptr;
+            c->cap_trace = 0;
+            CK(cudaHostAlloc((void **)&c->h_trace, words * sizeof(unsigned), cudaHostAllocMapped));
+            CK(cudaHostGetDevicePointer((void **)&c->d_trace, c->h_trace, 0));
+            c->cap_trace = words;
+        }
+        memset(c->h_trace, 0, c->cap_trace * sizeof(unsigned));
+        P.trace = c->d_trace;
+    }
 
     // signature of this launch: replay the captured graph when it repeats
     std::vector<unsigned char> sig(bytes + sizeof(P) + 2 * sizeof(int));
@@ -435,9 +461,11 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
         if (use_graph) CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemcpyAsync(c->d_meta, c->h_meta, bytes, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = rk_launch_init(std::min(grid, 4 * c->sms), &P, c->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(c->ev0, c->stream);
+        // inside a capture, only an external record becomes a timed event node
+        const unsigned evf = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev0, c->stream, evf);
         if (e == cudaSuccess) e = rk_launch_main(c->bh, grid, &P, c->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev1, c->stream, evf);
         if (use_graph) {
             cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
             if (e == cudaSuccess) e = e2;
@@ -482,6 +510,7 @@ extern "C" int recon_sync(recon_ctx *c)
     rk::Ctl h;
     CK(cudaMemcpy(&h, c->d_ctl, sizeof(h), cudaMemcpyDeviceToHost));
     c->last_err_tile = (h.err_tile == INT_MAX) ? -1 : h.err_tile;
+    c->last_abort = h.abort;
     if (h.abort) return RECON_ETIMEOUT;
     if (c->last_err_tile >= 0) return RECON_EMARKER;
     return RECON_OK;
@@ -772,4 +801,30 @@ extern "C" int recon_autotune(recon_ctx *c, const recon_tile *tiles, int n, int 
     c->bh = bb[0]; c->bands = bb[1]; c->k = bb[2];
     best[0] = bb[0]; best[1] = bb[1]; best[2] = bb[2];
     return RECON_OK;
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics
+
+extern "C" int recon_sync_for(recon_ctx *c, int timeout_ms)
+{
+    if (!c || timeout_ms < 0) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    for (long waited_us = 0;; waited_us += 200) {
+        const cudaError_t q = cudaStreamQuery(c->stream);
+        if (q == cudaSuccess) return recon_sync(c);
+        if (q != cudaErrorNotReady) return cuda_status(q);
+        if (waited_us / 1000 >= timeout_ms) return RECON_ETIMEOUT;
+        struct timespec ts = {0, 200000};
+        nanosleep(&ts, nullptr);
+    }
+}
+
+extern "C" int recon_trace(recon_ctx *c, unsigned *out, int n)
+{
+    if (!c || !out || n < 0) return -1;
+    if (!c->h_trace) return 0;
+    const int m = (int)std::min((size_t)n, c->cap_trace);
+    for (int i = 0; i < m; ++i) out[i] = ((volatile unsigned *)c->h_trace)[i];
+    return m;
 }

@@ -38,7 +38,8 @@ struct Ctl {
     unsigned long long head, tail;   // ring of re-queued blocks
     unsigned outstanding;            // blocks queued or running
     unsigned cold;                   // cursor into the packing order
-    int abort;                       // nonzero: a bounded wait ran out (RECON_ETIMEOUT)
+    int abort;                       // nonzero: a bound ran out (RECON_ETIMEOUT); the value says which
+    unsigned abort_block;            // block being processed when it ran out
     int err_tile;                    // lowest failing tile index (INT_MAX if none)
 };
 
@@ -63,6 +64,13 @@ struct Params {
     int bands;                     // warps scanning a block concurrently
     int phantom;                   // test: extra outstanding unit that never ends
     int check;                     // check J <= I on first visits
+    volatile unsigned *trace;      // optional: per-warp progress words in mapped host memory
+};
+
+// where-codes recorded in Ctl::abort when a bound runs out
+enum {
+    AB_RERUN = 1, AB_OVERFLOW = 2, AB_LEVELS = 3, AB_SCANS = 4, AB_CAS = 5, AB_NOTIFY = 6,
+    AB_RING = 7, AB_IDLE = 8, AB_PUSH = 9, AB_TMA = 10
 };
 
 }  // namespace rk

@@ -57,6 +57,7 @@ struct Smem {
     unsigned item, tile, flag, overflow, notify, visited;
     unsigned wn, wl;              // hand-back of a warp-only run of small levels
     unsigned phase;               // parity of the TMA barrier's next completion
+    unsigned abrt;                // block-uniform copy of the abort word
 };
 
 __device__ __forceinline__ int find_tile(const Params &P, unsigned b)
@@ -79,7 +80,20 @@ __device__ __forceinline__ unsigned cold_block(const Params &P, unsigned c)
     return P.tiles[P.order[lo]].block_base + (c - P.order_base[lo]);
 }
 
-__device__ void set_abort(const Params &P) { atomicExch(&P.ctl->abort, 1); }
+// Records the first bound that ran out (see AB_*); every CTA then winds down.
+__device__ void set_abort(const Params &P, int where)
+{
+    atomicCAS(&P.ctl->abort, 0, where);
+}
+
+__device__ __forceinline__ bool aborted(const Params &P) { return *(volatile int *)&P.ctl->abort != 0; }
+
+// progress trace (debug): lane 0 of each warp writes (code << 24 | block & 0xFFFFFF)
+__device__ __forceinline__ void trace(const Params &P, unsigned code, unsigned b)
+{
+    if (P.trace && (threadIdx.x & 31) == 0)
+        P.trace[blockIdx.x * (NT / 32) + (threadIdx.x >> 5)] = (code << 24) | (b & 0xFFFFFFu);
+}
 
 // Appends block b to the ring of re-queued blocks (the caller already moved
 // its state from IDLE to queued and counted it as outstanding).
@@ -88,7 +102,7 @@ __device__ void push_hot(const Params &P, unsigned b)
     unsigned long long t = atomicAdd(&P.ctl->tail, 1ull);
     unsigned *slot = &P.ring[t % P.nblocks];
     for (int it = 0; atomicCAS(slot, EMPTY, b) != EMPTY; ++it) {
-        if (it > (1 << 22)) { set_abort(P); return; }
+        if (it > (1 << 22)) { set_abort(P, AB_PUSH); return; }
         __nanosleep(64);
     }
 }
@@ -98,7 +112,8 @@ __device__ void notify_block(const Params &P, unsigned a)
 {
     unsigned old = *(volatile unsigned *)&P.state[a];
     unsigned nw;
-    for (;;) {
+    for (int it = 0;; ++it) {
+        if (it > (1 << 20)) { set_abort(P, AB_NOTIFY); return; }
         if (old & S_RUN) {
             if (old & S_DIRTY) return;
             nw = old | S_DIRTY;
@@ -132,7 +147,7 @@ __device__ unsigned next_item(const Params &P)
                 unsigned *slot = &P.ring[h % P.nblocks];
                 unsigned b;
                 for (int it = 0; (b = atomicExch(slot, EMPTY)) == EMPTY; ++it) {
-                    if (it > (1 << 22)) { set_abort(P); return EMPTY; }
+                    if (it > (1 << 22)) { set_abort(P, AB_RING); return EMPTY; }
                     __nanosleep(32);
                 }
                 return b;
@@ -146,7 +161,7 @@ __device__ unsigned next_item(const Params &P)
         if (*(volatile unsigned *)&c->outstanding == 0) return EMPTY;
         unsigned long long now = gtimer();
         if (idle0 == 0) idle0 = now;
-        else if ((long long)(now - idle0) > P.wait_ns) { set_abort(P); return EMPTY; }
+        else if ((long long)(now - idle0) > P.wait_ns) { set_abort(P, AB_IDLE); return EMPTY; }
         __nanosleep(sleep);
         if (sleep < 4096) sleep <<= 1;
     }
@@ -192,7 +207,7 @@ __device__ void tma_load_block(Smem<BH> &S, const Params &P, int t, int y0, int 
     for (long it = 0; !done; ++it) {
         asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
                      : "=r"(done) : "r"(bar), "r"(ph) : "memory");
-        if (!done && it > (1l << 26)) { set_abort(P); break; }
+        if (!done && it > (1l << 26)) { set_abort(P, AB_TMA); break; }
     }
     __syncthreads();
     if (threadIdx.x == 0) S.phase = ph ^ 1u;
@@ -528,20 +543,23 @@ __device__ __forceinline__ bool atomic_max_u8(uint32_t *Jw, unsigned off, uint32
     uint32_t *wp = Jw + (off >> 2);
     const unsigned sh = (off & 3) * 8;
     uint32_t old = *(volatile uint32_t *)wp;
-    for (;;) {
+    for (int it = 0; it < (1 << 20); ++it) {
         if (((old >> sh) & 0xFFu) >= v) return false;
         const uint32_t nw = (old & ~(0xFFu << sh)) | (v << sh);
         const uint32_t prev = atomicCAS(wp, old, nw);
         if (prev == old) return true;
         old = prev;
     }
+    return false;  // unreachable in practice: every failed CAS means another byte of the word moved
 }
 
 // Processes the wavefront level by level until it is empty (Algorithm 1's
 // propagation phase). n0 = size of level 0. Returns entries processed.
 template <int BH, int CONN>
-__device__ unsigned long long run_queue(Smem<BH> &S, uint16_t *gsp, unsigned n0)
+__device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *gsp, unsigned n0)
 {
+    constexpr long MAX_LEVELS = 1l << 21;
+    long levels = 0;
     constexpr int RB = PW * 4;  // bytes per shared row
     const int offs8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
     const int offs4[4] = {-RB, -1, 1, RB};
@@ -551,6 +569,10 @@ __device__ unsigned long long run_queue(Smem<BH> &S, uint16_t *gsp, unsigned n0)
     unsigned n = n0;
     int lvl = 0;
     while (n > 0) {
+        if (++levels > MAX_LEVELS) {
+            if (threadIdx.x == 0) set_abort(P, AB_LEVELS);
+            break;
+        }
         if (n <= 32) {
             // Small levels (thin fronts): warp 0 alone runs them with warp-level
             // synchronisation only, until a level grows past 64 entries or the
@@ -559,7 +581,13 @@ __device__ unsigned long long run_queue(Smem<BH> &S, uint16_t *gsp, unsigned n0)
                 const int lane = threadIdx.x & 31;
                 unsigned nn = n;
                 int l = lvl;
+                long wl = 0;
                 while (nn > 0 && nn <= 64) {
+                    if (++wl > MAX_LEVELS) {
+                        if (lane == 0) set_abort(P, AB_LEVELS);
+                        nn = 0;
+                        break;
+                    }
                     pops += nn;
                     unsigned total = 0;
                     for (unsigned base = 0; base < nn; base += 32) {
@@ -599,8 +627,12 @@ __device__ unsigned long long run_queue(Smem<BH> &S, uint16_t *gsp, unsigned n0)
         const unsigned navail = min(n, (unsigned)(QCAP + GCAP));
         pops += navail;
         // the slot being reset was last read before the previous barrier
-        if (threadIdx.x == 0) S.cnt[lvl ^ 1] = 0;
+        if (threadIdx.x == 0) {
+            S.cnt[lvl ^ 1] = 0;
+            S.abrt = (unsigned)*(volatile int *)&P.ctl->abort;
+        }
         __syncthreads();
+        if (S.abrt) break;
         for (unsigned base = 0; base < navail; base += NT) {
             const unsigned i = base + threadIdx.x;
             const bool act = i < navail;
@@ -683,6 +715,17 @@ __device__ void edge_notify_bits(Smem<BH> &S)
     if (bits) atomicOr(&S.notify, bits);
 }
 
+// Block-uniform read of the abort word.
+template <int BH>
+__device__ bool block_aborted(Smem<BH> &S, const Params &P)
+{
+    if (threadIdx.x == 0) S.abrt = (unsigned)*(volatile int *)&P.ctl->abort;
+    __syncthreads();
+    const bool a = S.abrt != 0;
+    __syncthreads();
+    return a;
+}
+
 // Returns true when the block's state was released here (normal path), false
 // when the caller must release it (tile failed the marker check).
 template <int BH, int CONN>
@@ -699,6 +742,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
     if (D.fast == 2) tma_load_block(S, P, t, y0, x0);
     else load_block(S, D, y0, x0, false);
     __syncthreads();
+    trace(P, 2, b);
 
     if (!visited && P.check) {
         bool bad = false;
@@ -723,23 +767,37 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
     bool need_seed = true;
     // a visited block sits at its fixed point for the halo it last saw
     bool frame_only = visited;
+    constexpr int MAX_SCAN_PAIRS = 1 << 16, MAX_RERUNS = 1 << 14, MAX_OVERFLOWS = 1 << 12;
     if (!visited || k < 0) {
-        const int pairs = k < 0 ? INT_MAX : k;
-        for (int s = 0; s < pairs; ++s) {
+        const int pairs = k < 0 ? MAX_SCAN_PAIRS : k;
+        int s = 0;
+        for (; s < pairs; ++s) {
             if (!scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) { if (k < 0) need_seed = false; break; }
         }
+        if (k < 0 && s == pairs && threadIdx.x == 0) set_abort(P, AB_SCANS);
     }
-    for (;;) {
+    trace(P, 3, b);
+    for (int rerun = 0;; ++rerun) {
+        if (rerun > MAX_RERUNS) {
+            if (threadIdx.x == 0) set_abort(P, AB_RERUN);
+            return true;
+        }
         if (need_seed) {
             unsigned n = frame_only ? seed_frame<BH, CONN>(S, gsp) : seed_pass<BH, CONN>(S, gsp);
             wk.seeds += 1;
-            wk.pops += run_queue<BH, CONN>(S, gsp, n);
-            while (S.overflow) {  // a level overflowed: rediscover the frontier
+            trace(P, 4, b);
+            wk.pops += run_queue<BH, CONN>(S, P, gsp, n);
+            for (int ov = 0; S.overflow; ++ov) {  // a level overflowed: rediscover the frontier
                 __syncthreads();
+                if (ov > MAX_OVERFLOWS) {
+                    if (threadIdx.x == 0) set_abort(P, AB_OVERFLOW);
+                    break;
+                }
                 n = seed_pass<BH, CONN>(S, gsp);
                 wk.seeds += 1;
-                wk.pops += run_queue<BH, CONN>(S, gsp, n);
+                wk.pops += run_queue<BH, CONN>(S, P, gsp, n);
             }
+            trace(P, 5, b);
         }
         __syncthreads();
         write_back(S, D, y0, x0);
@@ -764,14 +822,23 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
         save_edges(S);
         for (int i = threadIdx.x; i < BH / 32; i += NT) S.rowmask[i] = 0;
         __syncthreads();
+        trace(P, 6, b);
         if (!S.flag) return true;
+        if (block_aborted(S, P)) return true;
         __threadfence();
         load_block(S, D, y0, x0, true);  // fresh halo, then converge again
         wk.visits += 1;
         __syncthreads();
+        trace(P, 7, b);
         if (k < 0) {
             need_seed = false;
-            while (scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) {}
+            int sp = 0;
+            while (scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) {
+                if (++sp > MAX_SCAN_PAIRS) {
+                    if (threadIdx.x == 0) set_abort(P, AB_SCANS);
+                    break;
+                }
+            }
         } else {
             need_seed = true;
             frame_only = true;
@@ -800,16 +867,23 @@ __global__ void __launch_bounds__(NT) recon_persistent(Params P)
                 S.tile = (unsigned)t;
                 const unsigned old = atomicOr(&P.state[b], S_RUN | S_VIS);
                 S.visited = (old & S_VIS) ? 1u : 0u;
+                S.flag = (*(volatile int *)&P.tile_err[t] == 0) ? 1u : 0u;  // one read, shared
             }
         }
         __syncthreads();
         const unsigned b = S.item;
-        if (b == EMPTY) return;
+        if (b == EMPTY) {
+            trace(P, 15, 0);
+            return;
+        }
+        trace(P, 1, b);
         const int t = (int)S.tile;
         const TileDesc D = P.tiles[t];
         Work wk = {1, 0, 0, 0};
         bool released = false;
-        if (*(volatile int *)&P.tile_err[t] == 0) {
+        const bool live = S.flag != 0;
+        __syncthreads();  // S.flag is reused inside process_block
+        if (live) {
             if (D.conn == 8) released = process_block<BH, 8>(S, P, D, b, t, gsp, wk);
             else released = process_block<BH, 4>(S, P, D, b, t, gsp, wk);
         }
@@ -824,6 +898,7 @@ __global__ void __launch_bounds__(NT) recon_persistent(Params P)
             __threadfence();
             atomicSub(&P.ctl->outstanding, 1u);
         }
+        trace(P, 9, b);
     }
 }
 
@@ -845,6 +920,7 @@ __global__ void recon_init_kernel(Params P)
         P.ctl->outstanding = P.nblocks + (P.phantom ? 1u : 0u);
         P.ctl->cold = 0;
         P.ctl->abort = 0;
+        P.ctl->abort_block = 0;
         P.ctl->err_tile = INT_MAX;
     }
 }
