@@ -116,9 +116,11 @@ enum {
                                 are loaded into shared memory by TMA; 0 = plain loads */
     RECON_P_TRACE = 9,       /* diagnostics: 1 = kernels record per-warp progress in mapped
                                 host memory (read with recon_trace, even while running) */
-    RECON_P_LAST_ABORT = 10  /* read-only: which device-side bound ran out in the last call
+    RECON_P_LAST_ABORT = 10, /* read-only: which device-side bound ran out in the last call
                                 (0 = none; 1 rerun, 2 overflow, 3 levels, 4 scans, 5 CAS,
                                 6 notify, 7 ring slot, 8 idle wait, 9 ring push, 10 TMA) */
+    RECON_P_REVISIT_SCANS = 11  /* scan pairs a block runs when revisited (after a neighbour
+                                   raised its halo) before its queue phase; default 0 */
 };
 int recon_set_param(recon_ctx *ctx, int key, int64_t value);
 int64_t recon_get_param(recon_ctx *ctx, int key);
@@ -130,6 +132,8 @@ typedef struct {
     uint64_t scan_rows;   /* rows processed by raster / anti-raster scans */
     uint64_t pops;        /* queue entries processed */
     uint64_t seeds;       /* seeding passes over a block */
+    uint64_t levels;      /* wavefront levels processed (sequential steps of the queue phase) */
+    uint64_t busy_ns;     /* sum over block visits of the time a CTA spent on them */
 } recon_work;
 
 /* Waits at most timeout_ms for the context's stream: the device status as

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "librecon.so")
 RECON_OK, RECON_EINVAL, RECON_EMARKER, RECON_ENOMEM, RECON_ECUDA, RECON_ETIMEOUT = range(6)
 RECON_FLAG_SYNC, RECON_FLAG_NO_CHECK, RECON_FLAG_LEARNED, RECON_FLAG_NO_GRAPH = 1, 2, 4, 8
 (RECON_P_BLOCK_H, RECON_P_SWEEPS, RECON_P_GRID, RECON_P_BANDS, RECON_P_WAIT_NS, RECON_P_ORDER,
- RECON_P_TEST_STALL, RECON_P_TMA, RECON_P_TRACE, RECON_P_LAST_ABORT) = range(1, 11)
+ RECON_P_TEST_STALL, RECON_P_TMA, RECON_P_TRACE, RECON_P_LAST_ABORT, RECON_P_REVISIT_SCANS) = range(1, 12)
 
 # every symbol the header declares; tests check the library exports them all
 SYMBOLS = ("recon_init", "recon_run", "recon_batch", "recon_batch_ex", "recon_run_host",
@@ -39,7 +39,8 @@ class recon_tile(ctypes.Structure):
 
 class recon_work(ctypes.Structure):
     _fields_ = [("visits", ctypes.c_uint64), ("scan_rows", ctypes.c_uint64),
-                ("pops", ctypes.c_uint64), ("seeds", ctypes.c_uint64)]
+                ("pops", ctypes.c_uint64), ("seeds", ctypes.c_uint64), ("levels", ctypes.c_uint64),
+                ("busy_ns", ctypes.c_uint64)]
 
 
 class ReconError(RuntimeError):
@@ -171,7 +172,8 @@ def recon_get_work(ctx, n: int):
     rc = lib().recon_get_work(ctx, out, n)
     if rc != RECON_OK:
         raise ReconError(rc, "recon_get_work")
-    return [dict(visits=w.visits, scan_rows=w.scan_rows, pops=w.pops, seeds=w.seeds) for w in out[:n]]
+    return [dict(visits=w.visits, scan_rows=w.scan_rows, pops=w.pops, seeds=w.seeds, levels=w.levels,
+                 busy_ns=w.busy_ns) for w in out[:n]]
 
 
 def recon_last_kernel_ms(ctx) -> float:

@@ -28,7 +28,7 @@ struct recon_ctx {
     unsigned flags = 0;
     int sms = 0;
     // tunables
-    int bh = 64, k = 1, grid = 0, bands = 4, order_policy = 1, phantom = 0, use_tma = 1;
+    int bh = 64, k = 1, grid = 0, bands = 4, order_policy = 1, phantom = 0, use_tma = 1, revisit_scans = 0;
     long long wait_ns = 2000000000ll;
     // device scratch
     unsigned char *d_meta = nullptr; size_t cap_meta = 0;      // descriptors + order tables
@@ -200,6 +200,9 @@ extern "C" int recon_set_param(recon_ctx *c, int key, int64_t v)
     case RECON_P_TRACE:
         if (v != 0 && v != 1) return RECON_EINVAL;
         c->trace_on = (int)v; break;
+    case RECON_P_REVISIT_SCANS:
+        if (v < 0 || v > 16) return RECON_EINVAL;
+        c->revisit_scans = (int)v; break;
     default: return RECON_EINVAL;
     }
     drop_graph(c);
@@ -224,6 +227,7 @@ extern "C" int64_t recon_get_param(recon_ctx *c, int key)
     case RECON_P_TEST_STALL: return c->phantom;
     case RECON_P_TMA: return c->use_tma;
     case RECON_P_TRACE: return c->trace_on;
+    case RECON_P_REVISIT_SCANS: return c->revisit_scans;
     case RECON_P_LAST_ABORT: return c->last_abort;
     }
     return -1;
@@ -423,6 +427,7 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
     P.spill = c->d_spill;
     P.wait_ns = c->wait_ns;
     P.bands = c->bands;
+    P.revisit_scans = c->revisit_scans;
     P.phantom = c->phantom;
     P.check = (c->flags & RECON_FLAG_NO_CHECK) ? 0 : 1;
     P.trace = nullptr;
@@ -536,6 +541,8 @@ extern "C" int recon_get_work(recon_ctx *c, recon_work *out, int n)
         out[i].scan_rows = w[i].scan_rows;
         out[i].pops = w[i].pops;
         out[i].seeds = w[i].seeds;
+        out[i].levels = w[i].levels;
+        out[i].busy_ns = w[i].busy_ns;
     }
     return RECON_OK;
 }

@@ -44,7 +44,7 @@ struct Ctl {
 };
 
 struct Work {
-    unsigned long long visits, scan_rows, pops, seeds;
+    unsigned long long visits, scan_rows, pops, seeds, levels, busy_ns;
 };
 
 struct Params {
@@ -62,6 +62,7 @@ struct Params {
     uint16_t *spill;               // per CTA: 2 * GCAP entries
     long long wait_ns;             // limit of one idle wait
     int bands;                     // warps scanning a block concurrently
+    int revisit_scans;             // scan pairs a revisit runs before its queue phase
     int phantom;                   // test: extra outstanding unit that never ends
     int check;                     // check J <= I on first visits
     volatile unsigned *trace;      // optional: per-warp progress words in mapped host memory

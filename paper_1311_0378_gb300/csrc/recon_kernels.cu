@@ -53,7 +53,7 @@ struct Smem {
     uint8_t hIl[BH], hIr[BH];          // halo mask, left / right columns
     uint8_t eT[BW], eB[BW], eL[BH], eR[BH];  // edge values when neighbours last saw them
     unsigned rowmask[BH / 32];
-    unsigned cnt[2];              // sizes of the level being filled (two slots, by parity)
+    unsigned cq[3];               // level sizes, rotating by level (see run_queue)
     unsigned item, tile, flag, overflow, notify, visited;
     unsigned wn, wl;              // hand-back of a warp-only run of small levels
     unsigned phase;               // parity of the TMA barrier's next completion
@@ -451,7 +451,7 @@ __device__ __forceinline__ void warp_push(Smem<BH> &S, uint16_t *gsp, int lvl, b
     if (!bal) return;
     const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
     unsigned base = 0;
-    if (lane == leader) base = atomicAdd(&S.cnt[lvl], (unsigned)__popc(bal));
+    if (lane == leader) base = atomicAdd(&S.cq[lvl], (unsigned)__popc(bal));
     base = __shfl_sync(FULL, base, leader);
     if (pred) put_entry(S, gsp, lvl, base + __popc(bal & lanemask_lt()), v);
 }
@@ -461,7 +461,7 @@ __device__ __forceinline__ void warp_push(Smem<BH> &S, uint16_t *gsp, int lvl, b
 template <int BH, int CONN>
 __device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp)
 {
-    if (threadIdx.x == 0) { S.cnt[0] = 0; S.overflow = 0; }
+    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = lane + W0;
     for (int y = 1 + (threadIdx.x >> 5); y <= BH; y += NT / 32) {
@@ -485,7 +485,7 @@ __device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp)
             warp_push(S, gsp, 0, ((diff >> (8 * b)) & 0xFFu) != 0, (uint16_t)((y * PW + w) * 4 + b));
     }
     __syncthreads();
-    return S.cnt[0];
+    return S.cq[0];
 }
 
 // byte-wise atomic max on the shared J: returns true if it raised the byte
@@ -500,7 +500,7 @@ __device__ unsigned seed_frame(Smem<BH> &S, uint16_t *gsp)
 {
     constexpr int RB = PW * 4;
     constexpr int NFR = 2 * BW + 2 * (BH - 2);
-    if (threadIdx.x == 0) { S.cnt[0] = 0; S.overflow = 0; }
+    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; }
     __syncthreads();
     const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
     const uint8_t *Ib = (const uint8_t *)S.I;
@@ -534,7 +534,7 @@ __device__ unsigned seed_frame(Smem<BH> &S, uint16_t *gsp)
         warp_push(S, gsp, 0, raised, (uint16_t)p);
     }
     __syncthreads();
-    return S.cnt[0];
+    return S.cq[0];
 }
 
 
@@ -553,23 +553,96 @@ __device__ __forceinline__ bool atomic_max_u8(uint32_t *Jw, unsigned off, uint32
     return false;  // unreachable in practice: every failed CAS means another byte of the word moved
 }
 
+// Marks row r (0-based block row) in four per-thread register words.
+struct RowBits {
+    unsigned w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+    __device__ __forceinline__ void mark(unsigned r)
+    {
+        const unsigned bit = 1u << (r & 31);
+        switch (r >> 5) {
+        case 0: w0 |= bit; break;
+        case 1: w1 |= bit; break;
+        case 2: w2 |= bit; break;
+        default: w3 |= bit; break;
+        }
+    }
+    template <int BH>
+    __device__ __forceinline__ void flush(Smem<BH> &S)
+    {
+        if (w0) atomicOr(&S.rowmask[0], w0);
+        if (BH > 32 && w1) atomicOr(&S.rowmask[1 % (BH / 32)], w1);
+        if (BH > 64 && w2) atomicOr(&S.rowmask[2 % (BH / 32)], w2);
+        if (BH > 64 && w3) atomicOr(&S.rowmask[3 % (BH / 32)], w3);
+    }
+};
+
+// One pop of Algorithm 1's propagation phase for pixel offset p with current
+// value v: the neighbours q with J(q) < min(v, I(q)) (the propagation
+// condition) take that value (atomic byte max under the mask). All neighbour
+// tests are issued before any update; returns the mask of raised neighbours.
+template <int CONN>
+__device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t *Jb, const uint8_t *Ib,
+                                           unsigned p, uint32_t v, bool act, RowBits &rows)
+{
+    constexpr int RB = PW * 4;
+    const int off8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
+    const int off4[4] = {-RB, -1, 1, RB};
+    uint32_t cv[CONN];
+    unsigned cand = 0;
+#pragma unroll
+    for (int k = 0; k < CONN; ++k) {
+        const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
+        cv[k] = min(v, (uint32_t)Ib[q]);
+        if (act && Jb[q] < cv[k]) cand |= 1u << k;
+    }
+    unsigned raised = 0;
+#pragma unroll
+    for (int k = 0; k < CONN; ++k)
+        if ((cand >> k) & 1u) {
+            const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
+            if (atomic_max_u8(Jw, q, cv[k])) {
+                raised |= 1u << k;
+                rows.mark(q / RB - 1);
+            }
+        }
+    return raised;
+}
+
+// Warp-inclusive prefix sum of c.
+__device__ __forceinline__ unsigned warp_incl(unsigned c)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL, c, d);
+        if (lane >= d) c += t;
+    }
+    return c;
+}
+
 // Processes the wavefront level by level until it is empty (Algorithm 1's
-// propagation phase). n0 = size of level 0. Returns entries processed.
+// propagation phase). Level L reads queue L % 2 and appends to (L + 1) % 2;
+// its size is counted in cq[(L + 1) % 3], and cq[(L + 2) % 3] is reset during
+// level L, so one barrier per level suffices. n0 = size of level 0 (counted in
+// cq[0]; the seeding pass zeroed cq[1], cq[2]). Returns entries processed.
 template <int BH, int CONN>
-__device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *gsp, unsigned n0)
+__device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *gsp, unsigned n0,
+                                        unsigned long long &nlevels)
 {
     constexpr long MAX_LEVELS = 1l << 21;
-    long levels = 0;
-    constexpr int RB = PW * 4;  // bytes per shared row
-    const int offs8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
-    const int offs4[4] = {-RB, -1, 1, RB};
+    constexpr int RB = PW * 4;
+    const int off8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
+    const int off4[4] = {-RB, -1, 1, RB};
     const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
     const uint8_t *Ib = (const uint8_t *)S.I;
+    const int lane = threadIdx.x & 31;
+    const unsigned safe_p = RB + XOFF;   // an interior pixel for idle lanes
+    RowBits rows;
     unsigned long long pops = 0;
     unsigned n = n0;
-    int lvl = 0;
+    long L = 0;
     while (n > 0) {
-        if (++levels > MAX_LEVELS) {
+        if (L > MAX_LEVELS) {
             if (threadIdx.x == 0) set_abort(P, AB_LEVELS);
             break;
         }
@@ -578,85 +651,79 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
             // synchronisation only, until a level grows past 64 entries or the
             // front dies out; then all warps take over again.
             if ((threadIdx.x >> 5) == 0) {
-                const int lane = threadIdx.x & 31;
                 unsigned nn = n;
-                int l = lvl;
-                long wl = 0;
+                long l = L;
                 while (nn > 0 && nn <= 64) {
-                    if (++wl > MAX_LEVELS) {
+                    if (l > MAX_LEVELS) {
                         if (lane == 0) set_abort(P, AB_LEVELS);
                         nn = 0;
                         break;
                     }
                     pops += nn;
+                    ++nlevels;
+                    const int src = (int)(l & 1), dst = src ^ 1;
                     unsigned total = 0;
                     for (unsigned base = 0; base < nn; base += 32) {
                         const unsigned i = base + lane;
                         const bool act = i < nn;
-                        const unsigned p = act ? (unsigned)S.q[l][i] : 0u;
+                        const unsigned p = act ? (unsigned)S.q[src][i] : safe_p;
                         const uint32_t v = act ? Jb[p] : 0u;
+                        const unsigned raised = expand<CONN>(S.J, Jb, Ib, p, v, act, rows);
+                        const unsigned c = __popc(raised);
+                        const unsigned incl = warp_incl(c);
+                        unsigned o = total + incl - c;
 #pragma unroll
-                        for (int k = 0; k < CONN; ++k) {
-                            const unsigned q = p + (CONN == 8 ? offs8[k] : offs4[k]);
-                            bool raised = false;
-                            if (act) {
-                                const uint32_t c = min(v, (uint32_t)Ib[q]);
-                                if (Jb[q] < c && atomic_max_u8(S.J, q, c)) {
-                                    raised = true;
-                                    const unsigned row = q / RB;
-                                    atomicOr(&S.rowmask[(row - 1) >> 5], 1u << ((row - 1) & 31));
-                                }
-                            }
-                            const unsigned bal = __ballot_sync(FULL, raised);
-                            if (raised) S.q[l ^ 1][total + __popc(bal & lanemask_lt())] = (uint16_t)q;
-                            total += __popc(bal);
-                        }
+                        for (int k = 0; k < CONN; ++k)
+                            if ((raised >> k) & 1u) S.q[dst][o++] = (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k]));
+                        total += __shfl_sync(FULL, incl, 31);
                     }
                     __syncwarp();
                     nn = total;
-                    l ^= 1;
+                    ++l;
                 }
-                if (lane == 0) { S.wn = nn; S.wl = (unsigned)l; }
+                if (lane == 0) {
+                    S.wn = nn;
+                    S.wl = (unsigned)l;
+                    S.cq[(l + 1) % 3] = 0;
+                    S.cq[(l + 2) % 3] = 0;
+                }
             }
             __syncthreads();
             n = S.wn;
-            lvl = (int)S.wl;
+            L = (long)S.wl;
             __syncthreads();
             continue;
         }
         const unsigned navail = min(n, (unsigned)(QCAP + GCAP));
         pops += navail;
-        // the slot being reset was last read before the previous barrier
-        if (threadIdx.x == 0) {
-            S.cnt[lvl ^ 1] = 0;
-            S.abrt = (unsigned)*(volatile int *)&P.ctl->abort;
-        }
-        __syncthreads();
-        if (S.abrt) break;
+        ++nlevels;
+        const int src = (int)(L & 1), dst = src ^ 1;
+        const int cnext = (int)((L + 1) % 3);
+        if (threadIdx.x == 0) S.cq[(L + 2) % 3] = 0;   // last read two barriers ago
         for (unsigned base = 0; base < navail; base += NT) {
             const unsigned i = base + threadIdx.x;
             const bool act = i < navail;
-            const unsigned p = act ? get_entry(S, gsp, lvl, i) : 0u;
+            const unsigned p = act ? get_entry(S, gsp, src, i) : safe_p;
             const uint32_t v = act ? Jb[p] : 0u;
-#pragma unroll
-            for (int k = 0; k < CONN; ++k) {
-                const unsigned q = p + (CONN == 8 ? offs8[k] : offs4[k]);
-                bool raised = false;
-                if (act) {
-                    const uint32_t c = min(v, (uint32_t)Ib[q]);
-                    if (Jb[q] < c && atomic_max_u8(S.J, q, c)) {
-                        raised = true;
-                        const unsigned row = q / RB;
-                        atomicOr(&S.rowmask[(row - 1) >> 5], 1u << ((row - 1) & 31));
-                    }
-                }
-                warp_push(S, gsp, lvl ^ 1, raised, (uint16_t)q);
+            const unsigned raised = expand<CONN>(S.J, Jb, Ib, p, v, act, rows);
+            const unsigned c = __popc(raised);
+            const unsigned incl = warp_incl(c);
+            const unsigned tot = __shfl_sync(FULL, incl, 31);
+            unsigned b0 = 0;
+            if (tot) {
+                if (lane == 31) b0 = atomicAdd(&S.cq[cnext], tot);
+                b0 = __shfl_sync(FULL, b0, 31);
             }
+            unsigned o = b0 + incl - c;
+#pragma unroll
+            for (int k = 0; k < CONN; ++k)
+                if ((raised >> k) & 1u) put_entry(S, gsp, dst, o++, (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k])));
         }
         __syncthreads();
-        n = S.cnt[lvl ^ 1];
-        lvl ^= 1;
+        n = S.cq[cnext];
+        ++L;
     }
+    rows.flush(S);
     return pops;
 }
 
@@ -768,6 +835,11 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
     // a visited block sits at its fixed point for the halo it last saw
     bool frame_only = visited;
     constexpr int MAX_SCAN_PAIRS = 1 << 16, MAX_RERUNS = 1 << 14, MAX_OVERFLOWS = 1 << 12;
+    if (visited && k >= 0 && P.revisit_scans > 0) {
+        for (int s = 0; s < P.revisit_scans; ++s)
+            if (!scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) break;
+        frame_only = false;   // the scans moved interior pixels: seed from the whole block
+    }
     if (!visited || k < 0) {
         const int pairs = k < 0 ? MAX_SCAN_PAIRS : k;
         int s = 0;
@@ -786,7 +858,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
             unsigned n = frame_only ? seed_frame<BH, CONN>(S, gsp) : seed_pass<BH, CONN>(S, gsp);
             wk.seeds += 1;
             trace(P, 4, b);
-            wk.pops += run_queue<BH, CONN>(S, P, gsp, n);
+            wk.pops += run_queue<BH, CONN>(S, P, gsp, n, wk.levels);
             for (int ov = 0; S.overflow; ++ov) {  // a level overflowed: rediscover the frontier
                 __syncthreads();
                 if (ov > MAX_OVERFLOWS) {
@@ -795,7 +867,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
                 }
                 n = seed_pass<BH, CONN>(S, gsp);
                 wk.seeds += 1;
-                wk.pops += run_queue<BH, CONN>(S, P, gsp, n);
+                wk.pops += run_queue<BH, CONN>(S, P, gsp, n, wk.levels);
             }
             trace(P, 5, b);
         }
@@ -842,12 +914,17 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
         } else {
             need_seed = true;
             frame_only = true;
+            if (P.revisit_scans > 0) {
+                for (int s2 = 0; s2 < P.revisit_scans; ++s2)
+                    if (!scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) break;
+                frame_only = false;
+            }
         }
     }
 }
 
 template <int BH>
-__global__ void __launch_bounds__(NT) recon_persistent(Params P)
+__global__ void __launch_bounds__(NT, 6) recon_persistent(Params P)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<BH> &S = *reinterpret_cast<Smem<BH> *>(smem_raw);
@@ -879,7 +956,8 @@ __global__ void __launch_bounds__(NT) recon_persistent(Params P)
         trace(P, 1, b);
         const int t = (int)S.tile;
         const TileDesc D = P.tiles[t];
-        Work wk = {1, 0, 0, 0};
+        Work wk = {1, 0, 0, 0, 0, 0};
+        const unsigned long long t_start = gtimer();
         bool released = false;
         const bool live = S.flag != 0;
         __syncthreads();  // S.flag is reused inside process_block
@@ -895,6 +973,8 @@ __global__ void __launch_bounds__(NT) recon_persistent(Params P)
             atomicAdd(&P.work[t].scan_rows, wk.scan_rows);
             atomicAdd(&P.work[t].pops, wk.pops);
             atomicAdd(&P.work[t].seeds, wk.seeds);
+            atomicAdd(&P.work[t].levels, wk.levels);
+            atomicAdd(&P.work[t].busy_ns, gtimer() - t_start);
             __threadfence();
             atomicSub(&P.ctl->outstanding, 1u);
         }
@@ -912,7 +992,7 @@ __global__ void recon_init_kernel(Params P)
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)P.ntiles;
          i += (size_t)gridDim.x * blockDim.x) {
         P.tile_err[i] = 0;
-        P.work[i] = Work{0, 0, 0, 0};
+        P.work[i] = Work{0, 0, 0, 0, 0, 0};
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.ctl->head = 0;
