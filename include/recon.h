@@ -153,6 +153,22 @@ int recon_get_work(recon_ctx *ctx, recon_work *out, int n);
 int recon_last_kernel_ms(recon_ctx *ctx, float *ms);
 
 
+/* Allocation-free reconstruction of one tile (the paper has no counterpart:
+ * this serves callers that must not allocate device or pinned memory once
+ * running -- e.g. a plugin whose host framework owns all device memory through
+ * its own pool, or a latency-critical pipeline that cannot accept the implicit
+ * synchronisation an allocation may cause). No context is needed and nothing
+ * is allocated: the scratch space is one 11 MiB array compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits. I, J: device pointers, row stride = W, J <- R in place; runs on
+ * `cuda_stream` (NULL = the default stream) of the current device and waits
+ * for it. The first call on each device looks up the array's device address;
+ * make that first call outside any stream capture. Limits: at most 4096 blocks
+ * of 64 x 128 pixels (e.g. 4096 x 8192); larger inputs return RECON_EINVAL.
+ * Every call reuses the same array (cleared where it must start at zero), so
+ * calls that overlap on the GPU race: issue them one at a time. */
+int recon_run_noalloc(const uint8_t *I, uint8_t *J, int H, int W, int conn, void *cuda_stream);
+
 /* Autotuner: times every candidate block height {32, 64, 128} x bands
  * {1, 2, 4} x first-visit scan pairs {0, 1, 2} on this batch (each `reps`
  * times after one warm-up run, J restored from a device backup before every

@@ -28,7 +28,7 @@ SYMBOLS = ("recon_init", "recon_run", "recon_batch", "recon_batch_ex", "recon_ru
            "recon_strerror", "recon_set_param", "recon_get_param", "recon_get_work",
            "recon_last_kernel_ms", "recon_features", "recon_mlp_forward", "recon_mlp_grad",
            "recon_mlp_adam", "recon_mlp_train", "recon_sched_set_model", "recon_sched_plan_batch",
-           "recon_autotune", "recon_sync_for", "recon_trace")
+           "recon_autotune", "recon_sync_for", "recon_trace", "recon_run_noalloc")
 RECON_NFEAT, RECON_MLP_NPARAMS = 20, 5634
 
 
@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
         "recon_autotune": ([vp, tp, i, i, vp], i),
         "recon_sync_for": ([vp, i], i),
         "recon_trace": ([vp, vp, i], i),
+        "recon_run_noalloc": ([vp, vp, i, i, i, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -248,3 +249,8 @@ def recon_trace(ctx, n: int):
     out = (ctypes.c_uint * max(n, 1))()
     m = lib().recon_trace(ctx, out, n)
     return list(out[:max(m, 0)])
+
+
+def recon_run_noalloc(I: int, J: int, H: int, W: int, conn: int, stream: int = 0) -> int:
+    """Allocation-free single-tile reconstruction (device pointers; waits)."""
+    return lib().recon_run_noalloc(I, J, H, W, conn, ctypes.c_void_p(stream or None))
