@@ -134,6 +134,8 @@ typedef struct {
     uint64_t seeds;       /* seeding passes over a block */
     uint64_t levels;      /* wavefront levels processed (sequential steps of the queue phase) */
     uint64_t busy_ns;     /* sum over block visits of the time a CTA spent on them */
+    uint64_t phase_ns[6]; /* that time by phase: load, scans, seeding, queue,
+                             write-back + notification, and the work fetch before it */
 } recon_work;
 
 /* Waits at most timeout_ms for the context's stream: the device status as

@@ -40,7 +40,7 @@ class recon_tile(ctypes.Structure):
 class recon_work(ctypes.Structure):
     _fields_ = [("visits", ctypes.c_uint64), ("scan_rows", ctypes.c_uint64),
                 ("pops", ctypes.c_uint64), ("seeds", ctypes.c_uint64), ("levels", ctypes.c_uint64),
-                ("busy_ns", ctypes.c_uint64)]
+                ("busy_ns", ctypes.c_uint64), ("phase_ns", ctypes.c_uint64 * 6)]
 
 
 class ReconError(RuntimeError):
@@ -173,8 +173,9 @@ def recon_get_work(ctx, n: int):
     rc = lib().recon_get_work(ctx, out, n)
     if rc != RECON_OK:
         raise ReconError(rc, "recon_get_work")
+    names = ("load", "scan", "seed", "queue", "write", "fetch")
     return [dict(visits=w.visits, scan_rows=w.scan_rows, pops=w.pops, seeds=w.seeds, levels=w.levels,
-                 busy_ns=w.busy_ns) for w in out[:n]]
+                 busy_ns=w.busy_ns, phase_ns=dict(zip(names, list(w.phase_ns)))) for w in out[:n]]
 
 
 def recon_last_kernel_ms(ctx) -> float:

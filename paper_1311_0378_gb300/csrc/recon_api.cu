@@ -543,6 +543,7 @@ extern "C" int recon_get_work(recon_ctx *c, recon_work *out, int n)
         out[i].seeds = w[i].seeds;
         out[i].levels = w[i].levels;
         out[i].busy_ns = w[i].busy_ns;
+        for (int k = 0; k < 6; ++k) out[i].phase_ns[k] = w[i].phase_ns[k];
     }
     return RECON_OK;
 }

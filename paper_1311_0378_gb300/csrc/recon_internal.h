@@ -43,8 +43,13 @@ struct Ctl {
     int err_tile;                    // lowest failing tile index (INT_MAX if none)
 };
 
+// phase timers (ns, thread 0 of the CTA): load, scans, seeding, queue,
+// write-back + notification + release, work fetch
+enum { PH_LOAD = 0, PH_SCAN, PH_SEED, PH_QUEUE, PH_WRITE, PH_FETCH, NPH };
+
 struct Work {
     unsigned long long visits, scan_rows, pops, seeds, levels, busy_ns;
+    unsigned long long phase_ns[NPH];
 };
 
 struct Params {

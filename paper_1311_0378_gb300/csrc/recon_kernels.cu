@@ -55,7 +55,6 @@ struct Smem {
     unsigned rowmask[BH / 32];
     unsigned cq[3];               // level sizes, rotating by level (see run_queue)
     unsigned item, tile, flag, overflow, notify, visited;
-    unsigned wn, wl;              // hand-back of a warp-only run of small levels
     unsigned phase;               // parity of the TMA barrier's next completion
     unsigned abrt;                // block-uniform copy of the abort word
 };
@@ -459,12 +458,27 @@ __device__ __forceinline__ void warp_push(Smem<BH> &S, uint16_t *gsp, int lvl, b
 // Seeding pass: J(p) <- max(J(p), min(I(p), max over N(p) of J)) in place;
 // every raised pixel joins level 0. Returns the level's size.
 template <int BH, int CONN>
-__device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp)
+__device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp, bool changed_rows_only = false)
 {
+    // changed_rows_only: just the rows changed since the load and their
+    // neighbours (the verification after an atomic-free queue phase)
+    unsigned rm[BH / 32];
+#pragma unroll
+    for (int i = 0; i < BH / 32; ++i) rm[i] = S.rowmask[i];
+    __syncthreads();
     if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = lane + W0;
     for (int y = 1 + (threadIdx.x >> 5); y <= BH; y += NT / 32) {
+        if (changed_rows_only) {
+            bool act = false;
+#pragma unroll
+            for (int d = -1; d <= 1; ++d) {
+                const int r = y - 1 + d;   // 0-based block row
+                if (r >= 0 && r < BH && ((rm[r >> 5] >> (r & 31)) & 1u)) act = true;
+            }
+            if (!act) continue;
+        }
         const uint32_t *rw = &S.J[y * PW];
         const uint32_t c = rw[w];
         uint32_t m = vmax(c, vmax(west(rw[w - 1], c), east(c, rw[w + 1])));
@@ -526,7 +540,8 @@ __device__ unsigned seed_frame(Smem<BH> &S, uint16_t *gsp)
                 m = max(m, (uint32_t)Jb[p + RB + 1]);
             }
             const uint32_t nv = min(m, (uint32_t)Ib[p]);
-            if (nv > Jb[p] && atomic_max_u8(S.J, p, nv)) {
+            if (nv > Jb[p]) {   // one writer per frame pixel
+                ((volatile uint8_t *)S.J)[p] = (uint8_t)nv;
                 raised = true;
                 atomicOr(&S.rowmask[(r - 1) >> 5], 1u << ((r - 1) & 31));
             }
@@ -578,8 +593,11 @@ struct RowBits {
 
 // One pop of Algorithm 1's propagation phase for pixel offset p with current
 // value v: the neighbours q with J(q) < min(v, I(q)) (the propagation
-// condition) take that value (atomic byte max under the mask). All neighbour
-// tests are issued before any update; returns the mask of raised neighbours.
+// condition) take that value by a byte-wise atomic max under the mask. All
+// neighbour tests, then all first compare-and-swap attempts, are issued before
+// any result is awaited; only the rare attempt that lost a race on its word
+// retries. A neighbour counts as raised only if this thread's update stuck,
+// so each raise is pushed once. Returns the mask of raised neighbours.
 template <int CONN>
 __device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t *Jb, const uint8_t *Ib,
                                            unsigned p, uint32_t v, bool act, RowBits &rows)
@@ -595,12 +613,31 @@ __device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t 
         cv[k] = min(v, (uint32_t)Ib[q]);
         if (act && Jb[q] < cv[k]) cand |= 1u << k;
     }
+    uint32_t old[CONN], seen[CONN];
+#pragma unroll
+    for (int k = 0; k < CONN; ++k) {
+        const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
+        old[k] = ((cand >> k) & 1u) ? ((const volatile uint32_t *)Jw)[q >> 2] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < CONN; ++k) {
+        seen[k] = old[k];
+        if ((cand >> k) & 1u) {
+            const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
+            const unsigned sh = (q & 3) * 8;
+            if (((old[k] >> sh) & 0xFFu) < cv[k])
+                seen[k] = atomicCAS(Jw + (q >> 2), old[k], (old[k] & ~(0xFFu << sh)) | (cv[k] << sh));
+            else
+                cand &= ~(1u << k);   // someone raised it meanwhile
+        }
+    }
     unsigned raised = 0;
 #pragma unroll
     for (int k = 0; k < CONN; ++k)
         if ((cand >> k) & 1u) {
             const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
-            if (atomic_max_u8(Jw, q, cv[k])) {
+            const bool ok = (seen[k] == old[k]) || atomic_max_u8(Jw, q, cv[k]);
+            if (ok) {
                 raised |= 1u << k;
                 rows.mark(q / RB - 1);
             }
@@ -630,6 +667,9 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
                                         unsigned long long &nlevels)
 {
     constexpr long MAX_LEVELS = 1l << 21;
+    constexpr int RING = QCAP / (NT / 32);   // entries of one warp's private ring
+    constexpr int ASYNC_MAX = RING / 2;      // levels at most this large go to the rings
+    static_assert((RING & (RING - 1)) == 0, "ring size must be a power of two");
     constexpr int RB = PW * 4;
     const int off8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
     const int off4[4] = {-RB, -1, 1, RB};
@@ -646,53 +686,52 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
             if (threadIdx.x == 0) set_abort(P, AB_LEVELS);
             break;
         }
-        if (n <= 32) {
-            // Small levels (thin fronts): warp 0 alone runs them with warp-level
-            // synchronisation only, until a level grows past 64 entries or the
-            // front dies out; then all warps take over again.
-            if ((threadIdx.x >> 5) == 0) {
-                unsigned nn = n;
-                long l = L;
-                while (nn > 0 && nn <= 64) {
-                    if (l > MAX_LEVELS) {
-                        if (lane == 0) set_abort(P, AB_LEVELS);
-                        nn = 0;
-                        break;
-                    }
-                    pops += nn;
-                    ++nlevels;
-                    const int src = (int)(l & 1), dst = src ^ 1;
-                    unsigned total = 0;
-                    for (unsigned base = 0; base < nn; base += 32) {
-                        const unsigned i = base + lane;
-                        const bool act = i < nn;
-                        const unsigned p = act ? (unsigned)S.q[src][i] : safe_p;
-                        const uint32_t v = act ? Jb[p] : 0u;
-                        const unsigned raised = expand<CONN>(S.J, Jb, Ib, p, v, act, rows);
-                        const unsigned c = __popc(raised);
-                        const unsigned incl = warp_incl(c);
-                        unsigned o = total + incl - c;
+        if (n <= (unsigned)ASYNC_MAX) {
+            // Thin fronts: every warp takes a quarter of this level into a
+            // private ring (in the other queue buffer) and drains it on its
+            // own, in FIFO batches of up to 32 entries, with warp-level
+            // synchronisation only. Children go to the same warp's ring; a ring
+            // that would overflow drops entries and raises S.overflow (the
+            // caller then re-seeds the block).
+            const int src = (int)(L & 1);
+            const int warp = threadIdx.x >> 5;
+            uint16_t *ring = &S.q[src ^ 1][warp * RING];
+            const unsigned lo = (unsigned)warp * n / (NT / 32), hi = (unsigned)(warp + 1) * n / (NT / 32);
+            for (unsigned i = lo + lane; i < hi; i += 32) ring[i - lo] = S.q[src][i];
+            __syncwarp();
+            unsigned head = 0, tail = hi - lo;
+            long batches = 0;
+            while (head < tail) {
+                if (++batches > MAX_LEVELS) {
+                    if (lane == 0) set_abort(P, AB_LEVELS);
+                    break;
+                }
+                const unsigned m = min(tail - head, 32u);
+                const bool act = (unsigned)lane < m;
+                const unsigned p = act ? (unsigned)ring[(head + lane) & (RING - 1)] : safe_p;
+                const uint32_t v = act ? Jb[p] : 0u;
+                __syncwarp();
+                const unsigned raised = expand<CONN>(S.J, Jb, Ib, p, v, act, rows);
+                const unsigned c = __popc(raised);
+                const unsigned incl = warp_incl(c);
+                const unsigned tot = __shfl_sync(FULL, incl, 31);
+                if (tail + tot - (head + m) <= (unsigned)RING) {
+                    unsigned o = tail + incl - c;
 #pragma unroll
-                        for (int k = 0; k < CONN; ++k)
-                            if ((raised >> k) & 1u) S.q[dst][o++] = (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k]));
-                        total += __shfl_sync(FULL, incl, 31);
-                    }
-                    __syncwarp();
-                    nn = total;
-                    ++l;
+                    for (int k = 0; k < CONN; ++k)
+                        if ((raised >> k) & 1u)
+                            ring[(o++) & (RING - 1)] = (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k]));
+                    tail += tot;
+                } else if (lane == 0) {
+                    S.overflow = 1;
                 }
-                if (lane == 0) {
-                    S.wn = nn;
-                    S.wl = (unsigned)l;
-                    S.cq[(l + 1) % 3] = 0;
-                    S.cq[(l + 2) % 3] = 0;
-                }
+                head += m;
+                pops += m;
+                ++nlevels;
+                __syncwarp();
             }
             __syncthreads();
-            n = S.wn;
-            L = (long)S.wl;
-            __syncthreads();
-            continue;
+            break;
         }
         const unsigned navail = min(n, (unsigned)(QCAP + GCAP));
         pops += navail;
@@ -782,6 +821,19 @@ __device__ void edge_notify_bits(Smem<BH> &S)
     if (bits) atomicOr(&S.notify, bits);
 }
 
+// Phase clock of thread 0: adds the time since the last tick to wk.phase_ns[ph].
+struct PhaseClock {
+    unsigned long long last;
+    __device__ __forceinline__ void tick(Work &wk, int ph)
+    {
+        if (threadIdx.x == 0) {
+            const unsigned long long now = gtimer();
+            wk.phase_ns[ph] += now - last;
+            last = now;
+        }
+    }
+};
+
 // Block-uniform read of the abort word.
 template <int BH>
 __device__ bool block_aborted(Smem<BH> &S, const Params &P)
@@ -803,6 +855,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
     const int by = (int)(local / (unsigned)D.nbx), bx = (int)(local % (unsigned)D.nbx);
     const int y0 = by * BH, x0 = bx * BW;
     const bool visited = S.visited != 0;
+    PhaseClock clk{threadIdx.x == 0 ? gtimer() : 0ull};
 
     for (int i = threadIdx.x; i < BH / 32; i += NT) S.rowmask[i] = 0;
     if (threadIdx.x == 0) { S.notify = 0; S.flag = 0; }
@@ -829,6 +882,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
     }
     save_edges(S);
     __syncthreads();
+    clk.tick(wk, PH_LOAD);
 
     const int k = D.k;
     bool need_seed = true;
@@ -849,6 +903,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
         if (k < 0 && s == pairs && threadIdx.x == 0) set_abort(P, AB_SCANS);
     }
     trace(P, 3, b);
+    clk.tick(wk, PH_SCAN);
     for (int rerun = 0;; ++rerun) {
         if (rerun > MAX_RERUNS) {
             if (threadIdx.x == 0) set_abort(P, AB_RERUN);
@@ -858,6 +913,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
             unsigned n = frame_only ? seed_frame<BH, CONN>(S, gsp) : seed_pass<BH, CONN>(S, gsp);
             wk.seeds += 1;
             trace(P, 4, b);
+            clk.tick(wk, PH_SEED);
             wk.pops += run_queue<BH, CONN>(S, P, gsp, n, wk.levels);
             for (int ov = 0; S.overflow; ++ov) {  // a level overflowed: rediscover the frontier
                 __syncthreads();
@@ -870,6 +926,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
                 wk.pops += run_queue<BH, CONN>(S, P, gsp, n, wk.levels);
             }
             trace(P, 5, b);
+            clk.tick(wk, PH_QUEUE);
         }
         __syncthreads();
         write_back(S, D, y0, x0);
@@ -895,6 +952,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
         for (int i = threadIdx.x; i < BH / 32; i += NT) S.rowmask[i] = 0;
         __syncthreads();
         trace(P, 6, b);
+        clk.tick(wk, PH_WRITE);
         if (!S.flag) return true;
         if (block_aborted(S, P)) return true;
         __threadfence();
@@ -902,6 +960,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
         wk.visits += 1;
         __syncthreads();
         trace(P, 7, b);
+        clk.tick(wk, PH_LOAD);
         if (k < 0) {
             need_seed = false;
             int sp = 0;
@@ -920,6 +979,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
                 frame_only = false;
             }
         }
+        clk.tick(wk, PH_SCAN);
     }
 }
 
@@ -936,6 +996,7 @@ __global__ void __launch_bounds__(NT, 6) recon_persistent(Params P)
     }
     __syncthreads();
     for (;;) {
+        const unsigned long long t_fetch = threadIdx.x == 0 ? gtimer() : 0ull;
         if (threadIdx.x == 0) {
             const unsigned b = next_item(P);
             S.item = b;
@@ -956,8 +1017,9 @@ __global__ void __launch_bounds__(NT, 6) recon_persistent(Params P)
         trace(P, 1, b);
         const int t = (int)S.tile;
         const TileDesc D = P.tiles[t];
-        Work wk = {1, 0, 0, 0, 0, 0};
+        Work wk = {1, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}};
         const unsigned long long t_start = gtimer();
+        wk.phase_ns[PH_FETCH] = t_start - t_fetch;
         bool released = false;
         const bool live = S.flag != 0;
         __syncthreads();  // S.flag is reused inside process_block
@@ -975,6 +1037,8 @@ __global__ void __launch_bounds__(NT, 6) recon_persistent(Params P)
             atomicAdd(&P.work[t].seeds, wk.seeds);
             atomicAdd(&P.work[t].levels, wk.levels);
             atomicAdd(&P.work[t].busy_ns, gtimer() - t_start);
+            for (int ph = 0; ph < NPH; ++ph)
+                if (wk.phase_ns[ph]) atomicAdd(&P.work[t].phase_ns[ph], wk.phase_ns[ph]);
             __threadfence();
             atomicSub(&P.ctl->outstanding, 1u);
         }
@@ -992,7 +1056,7 @@ __global__ void recon_init_kernel(Params P)
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)P.ntiles;
          i += (size_t)gridDim.x * blockDim.x) {
         P.tile_err[i] = 0;
-        P.work[i] = Work{0, 0, 0, 0, 0, 0};
+        P.work[i] = Work{0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}};
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.ctl->head = 0;
