@@ -8,7 +8,10 @@ Pipeline (every step on the GPU goes through the C ABI):
      h-dome / fill-holes markers 50/50, 8-connectivity);
   2. labels measured by the method itself: each tile reconstructed alone with
      variant A (scan pairs to stability, no queue) and variant B (k scan pairs
-     then the queue), device time from CUDA events -> log(ms);
+     then the queue); the label is the log of the work the kernel reports for
+     the tile -- the summed time CTAs spent on its blocks -- because inside a
+     batch the tiles share the GPU, so work, not a tile's latency alone,
+     decides the makespan;
   3. features: recon_features (16-bin histogram of I - J, blob-pixel and
      zero-marker fractions, log sizes);
   4. training: recon_mlp_train (the library's forward / backward / Adam
@@ -61,41 +64,66 @@ def install(ctx, path: str = MODEL_PATH) -> dict:
     return meta
 
 
-def label_chunk(ctx, specs, seed, variants, torch, dev):
-    """Features and per-variant log device times of one chunk of tiles."""
+class Arena:
+    """Pinned host and device buffers reused across chunks of tiles."""
+
+    def __init__(self, torch, dev, max_px):
+        self.h = torch.empty(2 * max_px, dtype=torch.uint8).pin_memory()
+        self.d = torch.empty(3 * max_px, dtype=torch.uint8, device=dev)
+        self.max_px = max_px
+
+
+def label_chunk(ctx, specs, seed, variants, torch, arena):
+    """Features and per-variant log device times of one chunk of tiles, each
+    tile reconstructed alone (J restored from its pristine copy every run)."""
     import synth
     n = len(specs)
-    Ih = [torch.empty((s.H, s.W), dtype=torch.uint8).pin_memory() for s in specs]
-    Jh = [torch.empty((s.H, s.W), dtype=torch.uint8).pin_memory() for s in specs]
-    synth.generate_into(specs, seed, [x.data_ptr() for x in Ih], [x.data_ptr() for x in Jh])
-    Id = [x.to(dev, non_blocking=True) for x in Ih]
-    J0 = [x.to(dev, non_blocking=True) for x in Jh]
-    Jd = [x.clone() for x in J0]
+    px = [s.H * s.W for s in specs]
+    off = np.concatenate([[0], np.cumsum(px)]).astype(np.int64)
+    tot = int(off[-1])
+    assert tot <= arena.max_px
+    hI, hJ = arena.h[:tot], arena.h[tot:2 * tot]
+    synth.generate_into(specs, seed, [hI.data_ptr() + int(o) for o in off[:-1]],
+                        [hJ.data_ptr() + int(o) for o in off[:-1]])
+    dI, dJ0, dJ = arena.d[:tot], arena.d[tot:2 * tot], arena.d[2 * tot:3 * tot]
+    dI.copy_(hI, non_blocking=True)
+    dJ0.copy_(hJ, non_blocking=True)
+    dJ.copy_(dJ0)
     torch.cuda.synchronize()
-    tiles = [(a.data_ptr(), b.data_ptr(), s.H, s.W, s.W, s.conn) for a, b, s in zip(Id, Jd, specs)]
-    feat = torch.zeros((n, rc.RECON_NFEAT), dtype=torch.float32, device=dev)
+    tiles = [(dI.data_ptr() + int(off[t]), dJ.data_ptr() + int(off[t]), s.H, s.W, s.W, s.conn)
+             for t, s in enumerate(specs)]
+    feat = torch.zeros((n, rc.RECON_NFEAT), dtype=torch.float32, device=dI.device)
     rc.check(rc.recon_features(ctx, tiles, feat.data_ptr()), "recon_features")
+    work = np.zeros((n, len(variants)))
     ms = np.zeros((n, len(variants)))
-    work = []
     for t in range(n):
+        a, b = int(off[t]), int(off[t + 1])
         for v, var in enumerate(variants):
-            Jd[t].copy_(J0[t])
+            dJ[a:b].copy_(dJ0[a:b])
             torch.cuda.synchronize()
             rc.check(rc.recon_batch_ex(ctx, [tiles[t]], [var], None), "label run")
             ms[t, v] = rc.recon_last_kernel_ms(ctx)
-            work.append(rc.recon_get_work(ctx, 1)[0])
-    return feat.cpu().numpy(), np.log(np.maximum(ms, 1e-4)), work
+            work[t, v] = rc.recon_get_work(ctx, 1)[0]["busy_ns"] * 1e-6   # CTA-milliseconds
+    return feat.cpu().numpy(), np.log(np.maximum(work, 1e-4)), np.log(np.maximum(ms, 1e-4))
 
 
-def build_dataset(ctx, specs, seed, variants, chunk=64):
+def build_dataset(ctx, specs, seed, variants, chunk_px=1 << 30):
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
-    X, Y = [], []
-    for s in range(0, len(specs), chunk):
-        f, y, _ = label_chunk(ctx, specs[s:s + chunk], seed, variants, torch, dev)
+    arena = Arena(torch, dev, max(chunk_px, max(s.H * s.W for s in specs)))
+    X, Y, Yms = [], [], []
+    i = 0
+    while i < len(specs):
+        j, acc = i, 0
+        while j < len(specs) and acc + specs[j].H * specs[j].W <= arena.max_px:
+            acc += specs[j].H * specs[j].W
+            j += 1
+        f, y, yms = label_chunk(ctx, specs[i:j], seed, variants, torch, arena)
         X.append(f)
         Y.append(y)
-    return np.concatenate(X), np.concatenate(Y)
+        Yms.append(yms)
+        i = j
+    return np.concatenate(X), np.concatenate(Y), np.concatenate(Yms)
 
 
 def train(ctx, X: np.ndarray, Y: np.ndarray, epochs=200, batch=256, lr=2e-3, seed=0):
@@ -129,6 +157,51 @@ def init_params(rng) -> np.ndarray:
     return np.concatenate(out).astype(np.float32)
 
 
+def evaluate(ctx, model_path, workload="eval1000", reps=3):
+    """Learned vs plain schedule on one batch: device time of the persistent
+    launch, and byte equality of the two outputs."""
+    import torch
+    import synth
+    w = synth.workload(workload)
+    specs = list(w.tiles)
+    tot = sum(s.H * s.W for s in specs)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    hI = torch.empty(tot, dtype=torch.uint8).pin_memory()
+    hJ = torch.empty(tot, dtype=torch.uint8).pin_memory()
+    off = np.concatenate([[0], np.cumsum([s.H * s.W for s in specs])]).astype(np.int64)
+    synth.generate_into(specs, w.seed, [hI.data_ptr() + int(o) for o in off[:-1]],
+                        [hJ.data_ptr() + int(o) for o in off[:-1]])
+    dI = hI.to(dev)
+    dJ0 = hJ.to(dev)
+    dJ = dJ0.clone()
+    torch.cuda.synchronize()
+    tiles = [(dI.data_ptr() + int(off[t]), dJ.data_ptr() + int(off[t]), s.H, s.W, s.W, s.conn)
+             for t, s in enumerate(specs)]
+    install(ctx, model_path)
+    st, var, order, pred = rc.recon_sched_plan_batch(ctx, tiles)
+    rc.check(st, "plan")
+
+    def timed(fn):
+        out = []
+        for r in range(reps + 1):
+            dJ.copy_(dJ0)
+            torch.cuda.synchronize()
+            fn()
+            rc.check(rc.recon_sync(ctx), "sync")
+            if r:
+                out.append(rc.recon_last_kernel_ms(ctx))
+        return float(np.median(out))
+
+    ms_plain = timed(lambda: rc.check(rc.recon_batch(ctx, tiles), "plain"))
+    R_plain = dJ.clone()
+    ms_learned = timed(lambda: rc.check(rc.recon_batch_ex(ctx, tiles, var, order), "learned"))
+    same = bool(torch.equal(R_plain, dJ))
+    return {"workload": workload, "tiles": len(specs), "pixels": tot, "plain_ms": ms_plain,
+            "learned_ms": ms_learned, "plain_mpix_s": tot / ms_plain / 1e3, "learned_mpix_s": tot / ms_learned / 1e3,
+            "gain": ms_plain / ms_learned, "outputs_identical": same,
+            "variant_a_fraction": float(np.mean(np.array(var) == -1))}
+
+
 def main():
     import argparse
     import torch
@@ -138,25 +211,28 @@ def main():
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--out", default=MODEL_PATH)
     ap.add_argument("--queue-k", type=int, default=1)
+    ap.add_argument("--eval", action="store_true", help="then compare learned vs plain on eval1000")
     args = ap.parse_args()
     w = synth.workload("train20k")
     specs = list(w.tiles[:args.tiles])
     ctx = rc.recon_init(0, 0, 0)
     variants = (-1, args.queue_k)
     t0 = time.time()
-    X, Y = build_dataset(ctx, specs, w.seed, variants)
+    X, Y, Yms = build_dataset(ctx, specs, w.seed, variants)
     t1 = time.time()
     theta, norm, losses = train(ctx, X, Y, epochs=args.epochs)
     t2 = time.time()
     pick_b = float(np.mean(Y[:, 1] < Y[:, 0]))
     meta = {"tiles": len(specs), "workload": w.name, "seed": w.seed, "variants": list(variants),
-            "label": "log device ms of the tile reconstructed alone", "epochs": args.epochs,
+            "label": "log CTA-busy milliseconds (work) of the tile reconstructed alone", "epochs": args.epochs,
             "final_loss": losses[-1], "first_loss": losses[0], "label_seconds": round(t1 - t0, 1),
             "train_seconds": round(t2 - t1, 1), "fraction_b_faster": pick_b}
     save(args.out, theta, norm, variants, meta)
-    np.savez_compressed(os.path.splitext(args.out)[0] + "_data.npz", X=X, Y=Y)
+    np.savez_compressed(os.path.splitext(args.out)[0] + "_data.npz", X=X, Y=Y, Yms=Yms)
+    print(json.dumps(meta), flush=True)
+    if args.eval:
+        print(json.dumps(evaluate(ctx, args.out)), flush=True)
     rc.recon_free(ctx)
-    print(json.dumps(meta))
 
 
 if __name__ == "__main__":
