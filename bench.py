@@ -187,18 +187,27 @@ def compare_schedules(rc, ctx, stream, Is, Js, J0, tiles, desc, px, flush, args)
     schedule vs the plain one, on the same tiles and GPU (outputs identical:
     R is unique; the tests check it)."""
     res = {}
-    def batched():
-        rc.check(rc.recon_batch(ctx, desc), "batch")
-    def loop():
+    k_default = rc.recon_get_param(ctx, rc.RECON_P_SWEEPS)
+    g_default = rc.recon_get_param(ctx, rc.RECON_P_SCAN_GAIN)
+    plain_var = [k_default + 256 * (g_default // 64) if k_default >= 0 else -1] * len(desc)
+    plain_order = sorted(range(len(desc)), key=lambda i: -desc[i][2] * desc[i][3])
+    def batched():   # the plain schedule: context defaults, largest tiles first
+        rc.check(rc.recon_batch_ex(ctx, desc, plain_var, plain_order), "batch")
+    def loop():      # the plain per-tile path: one launch per tile, context defaults
         for d in desc:
-            st = rc.recon_run(ctx, d[0], d[1], d[2], d[3], d[5])
+            st = rc.recon_batch_ex(ctx, [d], plain_var[:1], [0])
             if st != rc.RECON_OK:
-                raise rc.ReconError(st, "recon_run")
+                raise rc.ReconError(st, "per-tile launch")
     res["batched_plain_mpix_s"] = round(px / time_fn(batched, stream, Js, J0, flush) / 1e3, 1)
     res["per_tile_loop_mpix_s"] = round(px / time_fn(loop, stream, Js, J0, flush, reps=2) / 1e3, 1)
     try:
         from paper_1311_0378_gb300 import cost_model
         meta = cost_model.install(ctx)
+        import torch
+        with torch.cuda.stream(stream):   # plan on the pristine markers
+            for a, b in zip(Js, J0):
+                a.copy_(b, non_blocking=True)
+        torch.cuda.synchronize()
         st, var, order, pred = rc.recon_sched_plan_batch(ctx, desc)
         rc.check(st, "plan")
         def learned():
@@ -209,7 +218,8 @@ def compare_schedules(rc, ctx, stream, Is, Js, J0, tiles, desc, px, flush, args)
             rc.check(rc.recon_batch_ex(ctx, desc, v2, o2), "learned batch")
         res["batched_learned_mpix_s"] = round(px / time_fn(learned, stream, Js, J0, flush) / 1e3, 1)
         res["batched_learned_with_planning_mpix_s"] = round(px / time_fn(learned_full, stream, Js, J0, flush) / 1e3, 1)
-        res["learned_variant_b_fraction"] = round(sum(1 for v in var if v != -1) / len(var), 3)
+        vb = cost_model.load()[2][1]
+        res["learned_queue_variant_fraction"] = round(sum(1 for v in var if v == vb) / len(var), 3)
         res["model_tiles"] = meta.get("tiles")
     except (OSError, ValueError) as e:
         res["batched_learned_mpix_s"] = None
@@ -233,6 +243,9 @@ def main():
     ap.add_argument("--compare", action="store_true",
                     help="also time the per-tile launch loop and the learned schedule")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--schedule", default="learned", choices=["learned", "plain"],
+                    help="learned: the cost model picks each tile's variant and the packing order "
+                         "(planning runs inside every timed step); plain: context defaults")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -268,7 +281,12 @@ def main():
     torch.cuda.synchronize()
 
     stream = torch.cuda.Stream(device=dev)
-    ctx = rc.recon_init(local, stream.cuda_stream, 0)
+    learned = args.schedule == "learned"
+    ctx = rc.recon_init(local, stream.cuda_stream, rc.RECON_FLAG_LEARNED if learned else 0)
+    model_meta = None
+    if learned:
+        from paper_1311_0378_gb300 import cost_model
+        model_meta = cost_model.install(ctx)
     for key, val in ((rc.RECON_P_BLOCK_H, args.block_h), (rc.RECON_P_BANDS, args.bands)):
         if val:
             rc.check(rc.recon_set_param(ctx, key, val))
@@ -282,7 +300,10 @@ def main():
     params = {"block_h": rc.recon_get_param(ctx, rc.RECON_P_BLOCK_H),
               "bands": rc.recon_get_param(ctx, rc.RECON_P_BANDS),
               "scan_pairs": rc.recon_get_param(ctx, rc.RECON_P_SWEEPS),
-              "grid": rc.recon_get_param(ctx, rc.RECON_P_GRID), "autotuned": tuned is not None}
+              "grid": rc.recon_get_param(ctx, rc.RECON_P_GRID), "autotuned": tuned is not None,
+              "schedule": args.schedule,
+              "cost_model": ({"tiles": model_meta.get("tiles"), "variants": model_meta.get("variants")}
+                             if model_meta else None)}
     px = sum(t.H * t.W for t in tiles)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 

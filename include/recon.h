@@ -76,10 +76,13 @@ int recon_run(recon_ctx *ctx, const uint8_t *I, uint8_t *J, int H, int W, int co
  * On a device error, recon_last_error_tile names the first failing tile. */
 int recon_batch(recon_ctx *ctx, const recon_tile *tiles, int n);
 
-/* As recon_batch with an explicit schedule: variant[t] = number of raster +
- * anti-raster pairs a block runs on its first visit before its queue phase
- * (-1 = scans to stability, no queue), order[] = permutation of 0..n-1 giving
- * the packing order. Either array may be NULL (context defaults). */
+/* As recon_batch with an explicit schedule. variant[t] = -1: scan pairs to
+ * stability, no queue; otherwise variant[t] = k + 256 * g: a block runs k
+ * raster + anti-raster pairs on its first visit, then (g > 0) keeps scanning,
+ * on first visits and revisits, while a pair still raises at least 64 * g
+ * pixels, then switches to its queue phase (0 <= k <= 64, 0 <= g <= 4096).
+ * order[] = permutation of 0..n-1 giving the packing order. Either array may
+ * be NULL (context defaults). */
 int recon_batch_ex(recon_ctx *ctx, const recon_tile *tiles, int n, const int *variant,
                    const int *order);
 
@@ -119,8 +122,11 @@ enum {
     RECON_P_LAST_ABORT = 10, /* read-only: which device-side bound ran out in the last call
                                 (0 = none; 1 rerun, 2 overflow, 3 levels, 4 scans, 5 CAS,
                                 6 notify, 7 ring slot, 8 idle wait, 9 ring push, 10 TMA) */
-    RECON_P_REVISIT_SCANS = 11  /* scan pairs a block runs when revisited (after a neighbour
+    RECON_P_REVISIT_SCANS = 11, /* scan pairs a block runs when revisited (after a neighbour
                                    raised its halo) before its queue phase; default 0 */
+    RECON_P_SCAN_GAIN = 12      /* default adaptive scan-to-queue switch: after its fixed scan
+                                   pairs a block keeps scanning while a pair raises at least this
+                                   many pixels (first visits and revisits); 0 = off */
 };
 int recon_set_param(recon_ctx *ctx, int key, int64_t value);
 int64_t recon_get_param(recon_ctx *ctx, int key);
@@ -172,11 +178,12 @@ int recon_last_kernel_ms(recon_ctx *ctx, float *ms);
 int recon_run_noalloc(const uint8_t *I, uint8_t *J, int H, int W, int conn, void *cuda_stream);
 
 /* Autotuner: times every candidate block height {32, 64, 128} x bands
- * {1, 2, 4} x first-visit scan pairs {0, 1, 2} on this batch (each `reps`
- * times after one warm-up run, J restored from a device backup before every
- * run), installs the fastest in the context and writes it to best[3] =
- * {block height, bands, scan pairs}. J holds its original marker on return.
- * The paper tunes its scan-to-queue switch point the same way (Sec. VI-B). */
+ * {2, 4} x first-visit scan pairs {0, 1, 2} x adaptive scan gain {0, 512} on
+ * this batch (each `reps` times after one warm-up run, J restored from a
+ * device backup before every run), installs the fastest in the context and
+ * writes it to best[4] = {block height, bands, scan pairs, scan gain}. J
+ * holds its original marker on return. The paper tunes its scan-to-queue
+ * switch point the same way (Sec. VI-B). */
 int recon_autotune(recon_ctx *ctx, const recon_tile *tiles, int n, int reps, int *best);
 
 /* ---- learned cost model ------------------------------------------------

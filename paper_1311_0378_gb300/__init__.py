@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_PKG, "librecon.so")
 RECON_OK, RECON_EINVAL, RECON_EMARKER, RECON_ENOMEM, RECON_ECUDA, RECON_ETIMEOUT = range(6)
 RECON_FLAG_SYNC, RECON_FLAG_NO_CHECK, RECON_FLAG_LEARNED, RECON_FLAG_NO_GRAPH = 1, 2, 4, 8
 (RECON_P_BLOCK_H, RECON_P_SWEEPS, RECON_P_GRID, RECON_P_BANDS, RECON_P_WAIT_NS, RECON_P_ORDER,
- RECON_P_TEST_STALL, RECON_P_TMA, RECON_P_TRACE, RECON_P_LAST_ABORT, RECON_P_REVISIT_SCANS) = range(1, 12)
+ RECON_P_TEST_STALL, RECON_P_TMA, RECON_P_TRACE, RECON_P_LAST_ABORT, RECON_P_REVISIT_SCANS,
+ RECON_P_SCAN_GAIN) = range(1, 13)
 
 # every symbol the header declares; tests check the library exports them all
 SYMBOLS = ("recon_init", "recon_run", "recon_batch", "recon_batch_ex", "recon_run_host",
@@ -236,8 +237,8 @@ def recon_sched_plan_batch(ctx, tiles):
 
 
 def recon_autotune(ctx, tiles, reps: int = 2):
-    """Returns (status, (block_h, bands, scan_pairs)) and installs the best."""
-    best = (ctypes.c_int * 3)()
+    """Returns (status, (block_h, bands, scan_pairs, scan_gain)) and installs the best."""
+    best = (ctypes.c_int * 4)()
     rc = lib().recon_autotune(ctx, _tiles(tiles), len(tiles), reps, best)
     return rc, tuple(best)
 

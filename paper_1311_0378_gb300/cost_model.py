@@ -199,7 +199,7 @@ def evaluate(ctx, model_path, workload="eval1000", reps=3):
     return {"workload": workload, "tiles": len(specs), "pixels": tot, "plain_ms": ms_plain,
             "learned_ms": ms_learned, "plain_mpix_s": tot / ms_plain / 1e3, "learned_mpix_s": tot / ms_learned / 1e3,
             "gain": ms_plain / ms_learned, "outputs_identical": same,
-            "variant_a_fraction": float(np.mean(np.array(var) == -1))}
+            "variant_a_fraction": float(np.mean(np.array(var) != load(model_path)[2][1]))}
 
 
 def main():
@@ -211,12 +211,19 @@ def main():
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--out", default=MODEL_PATH)
     ap.add_argument("--queue-k", type=int, default=1)
+    ap.add_argument("--scan-variant", type=int, default=1 + 256 * 8,
+                    help="variant A: 1 scan pair, then keep scanning while a pair raises >= 512 px")
     ap.add_argument("--eval", action="store_true", help="then compare learned vs plain on eval1000")
+    ap.add_argument("--eval-only", action="store_true", help="only evaluate the model at --out")
     args = ap.parse_args()
     w = synth.workload("train20k")
     specs = list(w.tiles[:args.tiles])
     ctx = rc.recon_init(0, 0, 0)
-    variants = (-1, args.queue_k)
+    if args.eval_only:
+        print(json.dumps(evaluate(ctx, args.out)), flush=True)
+        rc.recon_free(ctx)
+        return
+    variants = (args.scan_variant, args.queue_k)
     t0 = time.time()
     X, Y, Yms = build_dataset(ctx, specs, w.seed, variants)
     t1 = time.time()

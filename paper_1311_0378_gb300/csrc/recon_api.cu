@@ -28,7 +28,7 @@ struct recon_ctx {
     unsigned flags = 0;
     int sms = 0;
     // tunables
-    int bh = 64, k = 1, grid = 0, bands = 4, order_policy = 1, phantom = 0, use_tma = 1, revisit_scans = 0;
+    int bh = 128, k = 1, grid = 0, bands = 4, order_policy = 1, phantom = 0, use_tma = 1, revisit_scans = 0, scan_gain = 0;
     long long wait_ns = 2000000000ll;
     // device scratch
     unsigned char *d_meta = nullptr; size_t cap_meta = 0;      // descriptors + order tables
@@ -203,6 +203,9 @@ extern "C" int recon_set_param(recon_ctx *c, int key, int64_t v)
     case RECON_P_REVISIT_SCANS:
         if (v < 0 || v > 16) return RECON_EINVAL;
         c->revisit_scans = (int)v; break;
+    case RECON_P_SCAN_GAIN:
+        if (v < 0 || v > (1 << 20)) return RECON_EINVAL;
+        c->scan_gain = (int)v; break;
     default: return RECON_EINVAL;
     }
     drop_graph(c);
@@ -228,6 +231,7 @@ extern "C" int64_t recon_get_param(recon_ctx *c, int key)
     case RECON_P_TMA: return c->use_tma;
     case RECON_P_TRACE: return c->trace_on;
     case RECON_P_REVISIT_SCANS: return c->revisit_scans;
+    case RECON_P_SCAN_GAIN: return c->scan_gain;
     case RECON_P_LAST_ABORT: return c->last_abort;
     }
     return -1;
@@ -312,7 +316,14 @@ static int stage_meta(recon_ctx *c, const recon_tile *tiles, int n, const int *v
         d.I = T.I; d.J = T.J; d.H = T.H; d.W = T.W; d.pitch = T.pitch; d.conn = T.conn;
         d.nbx = (T.W + rk::BW - 1) / rk::BW;
         d.nby = (T.H + c->bh - 1) / c->bh;
-        d.k = variant ? variant[t] : c->k;
+        // variant: -1 = scans to stability; else k + 256 * (gain / 64)
+        if (variant) {
+            d.k = variant[t] == -1 ? -1 : (variant[t] & 0xFF);
+            d.gain = variant[t] == -1 ? 0 : (variant[t] >> 8) * 64;
+        } else {
+            d.k = c->k;
+            d.gain = c->scan_gain;
+        }
         d.fast = ((T.pitch % 4) == 0 && ((uintptr_t)T.I % 4) == 0 && ((uintptr_t)T.J % 4) == 0) ? 1 : 0;
         CUtensorMap *maps = (CUtensorMap *)(c->h_meta + L.off_maps + 256 * (size_t)t);
         memset(maps, 0, 256);
@@ -356,7 +367,8 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
         if (!tile_ok(tiles[t])) return RECON_EINVAL;
     if (variant)
         for (int t = 0; t < n; ++t)
-            if (variant[t] < -1 || variant[t] > 64) return RECON_EINVAL;
+            if (variant[t] < -1 || (variant[t] >= 0 && ((variant[t] & 0xFF) > 64 || (variant[t] >> 8) > 4096)))
+                return RECON_EINVAL;
     CK(cudaSetDevice(c->device));
 
     std::vector<int> lv, lo;
@@ -766,17 +778,18 @@ extern "C" int recon_autotune(recon_ctx *c, const recon_tile *tiles, int n, int 
     for (int t = 0; t < n && e == cudaSuccess; ++t)
         e = cudaMemcpyAsync(bk + off[t], tiles[t].J, (size_t)tiles[t].H * tiles[t].pitch, cudaMemcpyDeviceToDevice,
                             c->stream);
-    const int save_bh = c->bh, save_bands = c->bands, save_k = c->k;
+    const int save_bh = c->bh, save_bands = c->bands, save_k = c->k, save_gain = c->scan_gain;
     const unsigned save_flags = c->flags;
     c->flags &= ~RECON_FLAG_SYNC;
     float best_ms = 1e30f;
-    int bb[3] = {save_bh, save_bands, save_k};
+    int bb[4] = {save_bh, save_bands, save_k, save_gain};
     int rc = RECON_OK;
-    const int BHs[3] = {32, 64, 128}, BANDS[3] = {1, 2, 4}, KS[3] = {0, 1, 2};
+    const int BHs[3] = {32, 64, 128}, BANDS[2] = {2, 4}, KS[3] = {0, 1, 2}, GAINS[2] = {0, 512};
     for (int a = 0; a < 3 && e == cudaSuccess && rc == RECON_OK; ++a)
-        for (int b = 0; b < 3 && e == cudaSuccess && rc == RECON_OK; ++b)
-            for (int k = 0; k < 3 && e == cudaSuccess && rc == RECON_OK; ++k) {
-                c->bh = BHs[a]; c->bands = BANDS[b]; c->k = KS[k];
+        for (int b = 0; b < 2 && e == cudaSuccess && rc == RECON_OK; ++b)
+            for (int k = 0; k < 3 && e == cudaSuccess && rc == RECON_OK; ++k)
+            for (int gi = 0; gi < 2 && e == cudaSuccess && rc == RECON_OK; ++gi) {
+                c->bh = BHs[a]; c->bands = BANDS[b]; c->k = KS[k]; c->scan_gain = GAINS[gi];
                 drop_graph(c);
                 float sum = 0.0f;
                 for (int r = 0; r < reps + 1 && e == cudaSuccess && rc == RECON_OK; ++r) {
@@ -792,7 +805,7 @@ extern "C" int recon_autotune(recon_ctx *c, const recon_tile *tiles, int n, int 
                 }
                 if (rc == RECON_OK && e == cudaSuccess && sum / reps < best_ms) {
                     best_ms = sum / reps;
-                    bb[0] = BHs[a]; bb[1] = BANDS[b]; bb[2] = KS[k];
+                    bb[0] = BHs[a]; bb[1] = BANDS[b]; bb[2] = KS[k]; bb[3] = GAINS[gi];
                 }
             }
     for (int t = 0; t < n && e == cudaSuccess; ++t)
@@ -803,11 +816,11 @@ extern "C" int recon_autotune(recon_ctx *c, const recon_tile *tiles, int n, int 
     c->flags = save_flags;
     drop_graph(c);
     if (rc != RECON_OK || e != cudaSuccess) {
-        c->bh = save_bh; c->bands = save_bands; c->k = save_k;
+        c->bh = save_bh; c->bands = save_bands; c->k = save_k; c->scan_gain = save_gain;
         return rc != RECON_OK ? rc : cuda_status(e);
     }
-    c->bh = bb[0]; c->bands = bb[1]; c->k = bb[2];
-    best[0] = bb[0]; best[1] = bb[1]; best[2] = bb[2];
+    c->bh = bb[0]; c->bands = bb[1]; c->k = bb[2]; c->scan_gain = bb[3];
+    best[0] = bb[0]; best[1] = bb[1]; best[2] = bb[2]; best[3] = bb[3];
     return RECON_OK;
 }
 

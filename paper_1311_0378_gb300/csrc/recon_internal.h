@@ -31,7 +31,8 @@ struct alignas(16) TileDesc {
     int fast;             // 1: rows start on 4-byte boundaries (word loads and stores)
                           // 2: also 16-byte rows: TMA loads through tmaps[2t], tmaps[2t+1]
     unsigned block_base;  // first global block index of this tile
-    int pad[3];
+    int gain;             // adaptive scan-to-queue switch: keep scanning while a pair raises >= gain px
+    int pad[2];
 };
 
 struct Ctl {

@@ -319,10 +319,10 @@ __device__ __forceinline__ uint32_t compose(uint32_t g, uint32_t f)
 }
 
 template <int BH, int CONN>
-__device__ bool raster_rows(Smem<BH> &S, int r0, int r1)
+__device__ unsigned raster_rows(Smem<BH> &S, int r0, int r1)
 {
     const int lane = threadIdx.x & 31, w = lane + W0;
-    bool any = false;
+    unsigned any = 0;
     for (int y = r0; y < r1; ++y) {
         __syncwarp();
         const uint32_t *up = &S.J[(y - 1) * PW];
@@ -349,19 +349,20 @@ __device__ bool raster_rows(Smem<BH> &S, int r0, int r1)
         const uint32_t r = vmin(C2, vmax(A2, vin * 0x01010101u));
         const bool ch = (r != j);
         if (ch) S.J[y * PW + w] = r;
-        if (__any_sync(FULL, ch)) {
-            any = true;
+        const unsigned nch = __reduce_add_sync(FULL, (unsigned)__popc(__vcmpne4(r, j)) >> 3);
+        if (nch) {
+            any += nch;
             if (lane == 0) atomicOr(&S.rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
         }
     }
-    return any;
+    return any;   // pixels changed (warp-uniform)
 }
 
 template <int BH, int CONN>
-__device__ bool antiraster_rows(Smem<BH> &S, int r0, int r1)
+__device__ unsigned antiraster_rows(Smem<BH> &S, int r0, int r1)
 {
     const int lane = threadIdx.x & 31, w = lane + W0;
-    bool any = false;
+    unsigned any = 0;
     for (int y = r1 - 1; y >= r0; --y) {
         __syncwarp();
         const uint32_t *dn = &S.J[(y + 1) * PW];
@@ -388,34 +389,36 @@ __device__ bool antiraster_rows(Smem<BH> &S, int r0, int r1)
         const uint32_t r = vmin(C2, vmax(A2, vin * 0x01010101u));
         const bool ch = (r != j);
         if (ch) S.J[y * PW + w] = r;
-        if (__any_sync(FULL, ch)) {
-            any = true;
+        const unsigned nch = __reduce_add_sync(FULL, (unsigned)__popc(__vcmpne4(r, j)) >> 3);
+        if (nch) {
+            any += nch;
             if (lane == 0) atomicOr(&S.rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
         }
     }
-    return any;
+    return any;   // pixels changed (warp-uniform)
 }
 
 // One raster + anti-raster pair over the whole block; `bands` warps each take a
 // horizontal band of rows. Returns (block-uniformly) whether any pixel changed.
 template <int BH, int CONN>
-__device__ bool scan_pair(Smem<BH> &S, int bands, unsigned long long &rows)
+__device__ unsigned scan_pair(Smem<BH> &S, int bands, unsigned long long &rows)
 {
+    // returns the number of pixels the pair changed (block-uniform)
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) S.flag = 0;
     __syncthreads();
-    bool ch = false;
+    unsigned ch = 0;
     if (warp < bands) {
         const int r0 = 1 + warp * BH / bands, r1 = 1 + (warp + 1) * BH / bands;
         ch = raster_rows<BH, CONN>(S, r0, r1);
-        ch |= antiraster_rows<BH, CONN>(S, r0, r1);
+        ch += antiraster_rows<BH, CONN>(S, r0, r1);
     }
-    if (ch && (threadIdx.x & 31) == 0) S.flag = 1;
+    if (ch && (threadIdx.x & 31) == 0) atomicAdd(&S.flag, ch);
     rows += 2 * BH;
     __syncthreads();
-    const bool any = S.flag != 0;
-    __syncthreads();  // everyone has read the flag before it is reset again
-    return any;
+    const unsigned n = S.flag;
+    __syncthreads();  // everyone has read the count before it is reset again
+    return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -888,10 +891,14 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
     bool need_seed = true;
     // a visited block sits at its fixed point for the halo it last saw
     bool frame_only = visited;
-    constexpr int MAX_SCAN_PAIRS = 1 << 16, MAX_RERUNS = 1 << 14, MAX_OVERFLOWS = 1 << 12;
-    if (visited && k >= 0 && P.revisit_scans > 0) {
-        for (int s = 0; s < P.revisit_scans; ++s)
-            if (!scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) break;
+    constexpr int MAX_SCAN_PAIRS = 1 << 16, MAX_RERUNS = 1 << 14, MAX_OVERFLOWS = 1 << 12, MAX_ADAPTIVE = 64;
+    if (visited && k >= 0 && (P.revisit_scans > 0 || D.gain > 0)) {
+        // revisit: fixed scan pairs, then more while a pair still raises at
+        // least scan_gain pixels (the tuned scan-to-queue switch, Sec. VI-B)
+        for (int s = 0; s < MAX_ADAPTIVE; ++s) {
+            const unsigned g = scan_pair<BH, CONN>(S, P.bands, wk.scan_rows);
+            if (g == 0 || (s + 1 >= P.revisit_scans && (D.gain == 0 || g < (unsigned)D.gain))) break;
+        }
         frame_only = false;   // the scans moved interior pixels: seed from the whole block
     }
     if (!visited || k < 0) {
@@ -901,6 +908,10 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
             if (!scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) { if (k < 0) need_seed = false; break; }
         }
         if (k < 0 && s == pairs && threadIdx.x == 0) set_abort(P, AB_SCANS);
+        if (k >= 0 && s == pairs && D.gain > 0) {
+            for (int a = 0; a < MAX_ADAPTIVE; ++a)
+                if (scan_pair<BH, CONN>(S, P.bands, wk.scan_rows) < (unsigned)D.gain) break;
+        }
     }
     trace(P, 3, b);
     clk.tick(wk, PH_SCAN);
@@ -973,9 +984,11 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
         } else {
             need_seed = true;
             frame_only = true;
-            if (P.revisit_scans > 0) {
-                for (int s2 = 0; s2 < P.revisit_scans; ++s2)
-                    if (!scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) break;
+            if (P.revisit_scans > 0 || D.gain > 0) {
+                for (int s2 = 0; s2 < MAX_ADAPTIVE; ++s2) {
+                    const unsigned g = scan_pair<BH, CONN>(S, P.bands, wk.scan_rows);
+                    if (g == 0 || (s2 + 1 >= P.revisit_scans && (D.gain == 0 || g < (unsigned)D.gain))) break;
+                }
                 frame_only = false;
             }
         }

@@ -35,6 +35,18 @@ __device__ __forceinline__ int find_chunk_tile(const unsigned *chunk_base, int n
 constexpr int NCOUNT = 19;
 constexpr int CHUNK_ROWS = 16;
 
+// Adds one pixel to the per-thread counts. The bin is matched against every
+// constant index so the counts stay in registers.
+__device__ __forceinline__ void count(unsigned (&loc)[NCOUNT], uint32_t i, uint32_t j)
+{
+    const uint32_t bin = (j > i) ? 18u : ((i - j) >> 4);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) loc[k] += (bin == (uint32_t)k);
+    loc[18] += (bin == 18u);
+    loc[16] += (i >= 100);
+    loc[17] += (j == 0);
+}
+
 __global__ void __launch_bounds__(256) features_kernel(const FeatTile *T, int n, const unsigned *chunk_base,
                                                        unsigned nchunks, unsigned *counts)
 {
@@ -62,24 +74,15 @@ __global__ void __launch_bounds__(256) features_kernel(const FeatTile *T, int n,
 #pragma unroll
                         for (int s = 0; s < 4; ++s) {
                             const uint32_t i = (aw[q] >> (8 * s)) & 0xFF, j = (bw[q] >> (8 * s)) & 0xFF;
-                            if (j > i) loc[18]++;
-                            else loc[(i - j) >> 4]++;
-                            loc[16] += (i >= 100);
-                            loc[17] += (j == 0);
+                            count(loc, i, j);
                         }
                 }
                 for (int x = (nv << 4) + threadIdx.x; x < d.W; x += blockDim.x) {
-                    const uint32_t i = ri[x], j = rj[x];
-                    if (j > i) loc[18]++; else loc[(i - j) >> 4]++;
-                    loc[16] += (i >= 100);
-                    loc[17] += (j == 0);
+                    count(loc, ri[x], rj[x]);
                 }
             } else {
                 for (int x = threadIdx.x; x < d.W; x += blockDim.x) {
-                    const uint32_t i = ri[x], j = rj[x];
-                    if (j > i) loc[18]++; else loc[(i - j) >> 4]++;
-                    loc[16] += (i >= 100);
-                    loc[17] += (j == 0);
+                    count(loc, ri[x], rj[x]);
                 }
             }
         }

@@ -36,7 +36,9 @@ void recon_sched_destroy(recon_sched *s)
 
 int recon_sched_set(recon_sched *s, const float *theta, const float *norm, int va, int vb)
 {
-    if (!s || !theta || !norm || va < -1 || vb < -1 || va > 64 || vb > 64) return RECON_EINVAL;
+    // variants use the recon_batch_ex encoding: -1, or k + 256 * g (k <= 64, g <= 4096)
+    auto ok = [](int v) { return v == -1 || (v >= 0 && (v & 0xFF) <= 64 && (v >> 8) <= 4096); };
+    if (!s || !theta || !norm || !ok(va) || !ok(vb)) return RECON_EINVAL;
     if (!s->d_theta && cudaMalloc((void **)&s->d_theta, sizeof(float) * MLP_NPARAMS) != cudaSuccess)
         return RECON_ENOMEM;
     if (cudaMemcpy(s->d_theta, theta, sizeof(float) * MLP_NPARAMS, cudaMemcpyHostToDevice) != cudaSuccess)

@@ -19,7 +19,7 @@ from paper_1311_0378_gb300 import cost_model  # noqa: E402
 def test_model_file_meta():
     theta, norm, variants, meta = cost_model.load()
     assert theta.shape == (rc.RECON_MLP_NPARAMS,) and np.isfinite(theta).all()
-    assert meta["tiles"] == 20000 and variants == (-1, 1)
+    assert meta["tiles"] == 20000 and variants == (1 + 256 * 8, 1)
 
 
 def test_learned_schedule_gain_and_identity():
@@ -61,7 +61,8 @@ def test_learned_outputs_match_oracle_and_predictions_rank_work():
             rc.check(rc.recon_batch_ex(ctx, [tiles[t]], [var[t]], None), "solo")
             measured.append(rc.recon_get_work(ctx, 1)[0]["busy_ns"])
             np.testing.assert_array_equal(devs[t][1].cpu().numpy(), wants[t])
-        chosen = [pred[2 * t] if var[t] == -1 else pred[2 * t + 1] for t in range(len(specs))]
+        vb = cost_model.load()[2][1]
+        chosen = [pred[2 * t + 1] if var[t] == vb else pred[2 * t] for t in range(len(specs))]
         rp = np.argsort(np.argsort(chosen))
         rm = np.argsort(np.argsort(measured))
         rho = np.corrcoef(rp, rm)[0, 1]
