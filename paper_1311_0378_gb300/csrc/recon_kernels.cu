@@ -36,12 +36,6 @@ __device__ __forceinline__ unsigned long long gtimer()
     return t;
 }
 
-__device__ __forceinline__ uint32_t vmax(uint32_t a, uint32_t b) { return __vmaxu4(a, b); }
-__device__ __forceinline__ uint32_t vmin(uint32_t a, uint32_t b) { return __vminu4(a, b); }
-// pixel x-1 of each byte lane, taking lane 0's from the previous word's top byte
-__device__ __forceinline__ uint32_t west(uint32_t prev, uint32_t cur) { return __funnelshift_l(prev, cur, 8); }
-// pixel x+1 of each byte lane, taking lane 3's from the next word's low byte
-__device__ __forceinline__ uint32_t east(uint32_t cur, uint32_t next) { return __funnelshift_r(cur, next, 8); }
 
 template <int BH>
 struct Smem {
@@ -309,93 +303,140 @@ __device__ void save_edges(Smem<BH> &S)
 // ---------------------------------------------------------------------------
 // scans: one warp over rows [r0, r1) of the block (shared-memory row indices)
 
-__device__ __forceinline__ uint32_t map_pack(uint32_t A, uint32_t C) { return A | (C << 8); }
 
-// composition g o f of clamp maps v -> min(C, max(A, v)); g = (A, C) applied after f = (fA, fC)
+// Two-plane byte arithmetic. A shared-memory word holds pixels x..x+3 in
+// bytes 0..3; the scans work on its even plane E (pixels x, x+2 as two u16
+// lanes) and odd plane O (pixels x+1, x+3), where max / min are native u16x2
+// instructions (the byte-wise __vmaxu4 / __vminu4 are emulated).
+__device__ __forceinline__ uint32_t pmax(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t pmin(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t even_plane(uint32_t w) { return __byte_perm(w, 0u, 0x4240); }
+__device__ __forceinline__ uint32_t odd_plane(uint32_t w) { return __byte_perm(w, 0u, 0x4341); }
+__device__ __forceinline__ uint32_t merge_planes(uint32_t e, uint32_t o) { return __byte_perm(e, o, 0x6240); }
+// clamp-map composition f o g on both u16 lanes, f = (fA, fC), g = (gA, gC)
+__device__ __forceinline__ void pcompose(uint32_t fA, uint32_t fC, uint32_t gA, uint32_t gC, uint32_t &A, uint32_t &C)
+{
+    A = pmin(fC, pmax(fA, gA));
+    C = pmin(fC, pmax(fA, gC));
+}
+
+// A clamp map v -> min(C, max(A, v)) packed as A | C << 16 (one per lane of a
+// row); g o f on such packed maps is two byte broadcasts and two u16x2 ops.
+__device__ __forceinline__ uint32_t map_pack(uint32_t A, uint32_t C) { return A | (C << 16); }
 __device__ __forceinline__ uint32_t compose(uint32_t g, uint32_t f)
 {
-    const uint32_t A = g & 0xFF, C = g >> 8, fA = f & 0xFF, fC = f >> 8;
-    return map_pack(min(C, max(A, fA)), min(C, max(A, fC)));
+    const uint32_t A2 = __byte_perm(g, 0u, 0x4040), C2 = __byte_perm(g, 0u, 0x4242);
+    return pmin(C2, pmax(A2, f));
+}
+
+// Row recurrence of the scans. The previous row's result stays in registers
+// (the neighbouring lanes' planes arrive by shuffle, the halo words by a
+// broadcast load), and the next row's mask and marker words are loaded while
+// the current row is computed.
+template <int CONN, bool DOWN>
+__device__ __forceinline__ unsigned scan_rows(uint32_t *SJ, const uint32_t *SI, unsigned *rowmask, int r0, int r1)
+{
+    const int lane = threadIdx.x & 31, w = lane + W0;
+    const int step = DOWN ? 1 : -1;
+    const int yb = DOWN ? r0 : r1 - 1, ye = DOWN ? r1 : r0 - 1;
+    constexpr uint32_t ID_C = 0x00FF00FFu;    // identity map: A = 0, C = 255 (both lanes)
+    unsigned any = 0;
+    __syncwarp();
+    const uint32_t pw0 = SJ[(yb - step) * PW + w];
+    uint32_t pE = even_plane(pw0), pO = odd_plane(pw0);
+    uint32_t j = SJ[yb * PW + w], i = SI[yb * PW + w];
+    for (int y = yb; y != ye; y += step) {
+        const int yn = y + step;
+        uint32_t jn = 0, in = 0;
+        if (yn != ye) {
+            jn = SJ[yn * PW + w];
+            in = SI[yn * PW + w];
+        }
+        uint32_t vE = pE, vO = pO;
+        if (CONN == 8) {
+            const int yp = y - step;
+            uint32_t oW = __shfl_up_sync(FULL, pO, 1);     // odd plane of the word to the left
+            uint32_t eE = __shfl_down_sync(FULL, pE, 1);   // even plane of the word to the right
+            if (lane == 0) oW = odd_plane(SJ[yp * PW + WL]);
+            if (lane == 31) eE = even_plane(SJ[yp * PW + WR]);
+            const uint32_t westE = __funnelshift_l(oW, pO, 16);   // pixels x-1, x+1 of the even pixels
+            const uint32_t eastO = __funnelshift_r(pE, eE, 16);   // pixels x+2, x+4 of the odd pixels
+            vE = __vimax3_u16x2(pE, westE, pO);
+            vO = __vimax3_u16x2(pO, pE, eastO);
+        }
+        const uint32_t jE = even_plane(j), jO = odd_plane(j), iE = even_plane(i), iO = odd_plane(i);
+        const uint32_t aE = pmin(iE, pmax(jE, vE)), aO = pmin(iO, pmax(jO, vO));
+        uint32_t AE, CE, AO, CO;   // prefix clamp maps of every pixel inside the word
+        uint32_t m;
+        if (DOWN) {   // left to right: pixel order E.l0, O.l0, E.l1, O.l1
+            uint32_t A1O, C1O, A1E, C1E;
+            pcompose(aO, iO, aE, iE, A1O, C1O);                          // x+1 o x, x+3 o x+2
+            pcompose(aE, iE, aO << 16, (iO << 16) | 0x00FFu, A1E, C1E);   // x o id, x+2 o x+1
+            pcompose(A1E, C1E, A1E << 16, (C1E << 16) | 0x00FFu, AE, CE);
+            pcompose(A1O, C1O, A1O << 16, (C1O << 16) | 0x00FFu, AO, CO);
+            m = (AO >> 16) | (CO & 0xFFFF0000u);
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(FULL, m, d);
+                if (lane >= d) m = compose(m, o);
+            }
+        } else {      // right to left: pixel order O.l1, E.l1, O.l0, E.l0
+            uint32_t A1E, C1E, A1O, C1O;
+            pcompose(aE, iE, aO, iO, A1E, C1E);                               // x o x+1, x+2 o x+3
+            pcompose(aO, iO, aE >> 16, (iE >> 16) | 0x00FF0000u, A1O, C1O);    // x+1 o x+2, x+3 o id
+            pcompose(A1E, C1E, A1E >> 16, (C1E >> 16) | 0x00FF0000u, AE, CE);
+            pcompose(A1O, C1O, A1O >> 16, (C1O >> 16) | 0x00FF0000u, AO, CO);
+            m = (AE & 0xFFFFu) | (CE << 16);
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_down_sync(FULL, m, d);
+                if (lane + d < 32) m = compose(m, o);
+            }
+        }
+        (void)ID_C;
+        uint32_t ex = DOWN ? __shfl_up_sync(FULL, m, 1) : __shfl_down_sync(FULL, m, 1);
+        if (lane == (DOWN ? 0 : 31)) ex = map_pack(0, 255);
+        // the row's halo pixel on the side the scan starts from (x = -1 or x = BW)
+        const uint32_t h = DOWN ? (SJ[y * PW + WL] >> 24) : (SJ[y * PW + WR] & 0xFF);
+        const uint32_t vin = min(ex >> 16, max(ex & 0xFFFFu, h)) * 0x00010001u;
+        const uint32_t rE = pmin(CE, pmax(AE, vin)), rO = pmin(CO, pmax(AO, vin));
+        const uint32_t dE = rE ^ jE, dO = rO ^ jO;
+        const unsigned nd = ((dE & 0xFFFFu) != 0) + ((dE >> 16) != 0) + ((dO & 0xFFFFu) != 0) + ((dO >> 16) != 0);
+        if (nd) SJ[y * PW + w] = merge_planes(rE, rO);
+        const unsigned nch = __reduce_add_sync(FULL, nd);
+        if (nch) {
+            any += nch;
+            if (lane == 0) atomicOr(&rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
+        }
+        pE = rE;
+        pO = rO;
+        j = jn;
+        i = in;
+    }
+    __syncwarp();
+    return any;   // pixels changed (warp-uniform)
 }
 
 template <int BH, int CONN>
 __device__ unsigned raster_rows(Smem<BH> &S, int r0, int r1)
 {
-    const int lane = threadIdx.x & 31, w = lane + W0;
-    unsigned any = 0;
-    for (int y = r0; y < r1; ++y) {
-        __syncwarp();
-        const uint32_t *up = &S.J[(y - 1) * PW];
-        const uint32_t u = up[w];
-        uint32_t vert = u;
-        if (CONN == 8) vert = vmax(vert, vmax(west(up[w - 1], u), east(u, up[w + 1])));
-        const uint32_t j = S.J[y * PW + w], i = S.I[y * PW + w];
-        const uint32_t a = vmin(i, vmax(j, vert));
-        // per-byte clamp maps (a, i), composed left to right inside the word
-        const uint32_t A1 = vmin(i, vmax(a, a << 8));
-        const uint32_t C1 = vmin(i, vmax(a, (i << 8) | 0xFFu));
-        const uint32_t A2 = vmin(C1, vmax(A1, A1 << 16));
-        const uint32_t C2 = vmin(C1, vmax(A1, (C1 << 16) | 0xFFFFu));
-        uint32_t m = map_pack(A2 >> 24, C2 >> 24);
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t o = __shfl_up_sync(FULL, m, d);
-            if (lane >= d) m = compose(m, o);
-        }
-        uint32_t ex = __shfl_up_sync(FULL, m, 1);
-        if (lane == 0) ex = map_pack(0, 255);
-        const uint32_t h = S.J[y * PW + WL] >> 24;  // pixel x = -1 of this row (halo)
-        const uint32_t vin = min(ex >> 8, max(ex & 0xFF, h));
-        const uint32_t r = vmin(C2, vmax(A2, vin * 0x01010101u));
-        const bool ch = (r != j);
-        if (ch) S.J[y * PW + w] = r;
-        const unsigned nch = __reduce_add_sync(FULL, (unsigned)__popc(__vcmpne4(r, j)) >> 3);
-        if (nch) {
-            any += nch;
-            if (lane == 0) atomicOr(&S.rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
-        }
-    }
-    return any;   // pixels changed (warp-uniform)
+    return scan_rows<CONN, true>(S.J, S.I, S.rowmask, r0, r1);
 }
 
 template <int BH, int CONN>
 __device__ unsigned antiraster_rows(Smem<BH> &S, int r0, int r1)
 {
-    const int lane = threadIdx.x & 31, w = lane + W0;
-    unsigned any = 0;
-    for (int y = r1 - 1; y >= r0; --y) {
-        __syncwarp();
-        const uint32_t *dn = &S.J[(y + 1) * PW];
-        const uint32_t d = dn[w];
-        uint32_t vert = d;
-        if (CONN == 8) vert = vmax(vert, vmax(west(dn[w - 1], d), east(d, dn[w + 1])));
-        const uint32_t j = S.J[y * PW + w], i = S.I[y * PW + w];
-        const uint32_t a = vmin(i, vmax(j, vert));
-        // composed right to left inside the word
-        const uint32_t A1 = vmin(i, vmax(a, a >> 8));
-        const uint32_t C1 = vmin(i, vmax(a, (i >> 8) | 0xFF000000u));
-        const uint32_t A2 = vmin(C1, vmax(A1, A1 >> 16));
-        const uint32_t C2 = vmin(C1, vmax(A1, (C1 >> 16) | 0xFFFF0000u));
-        uint32_t m = map_pack(A2 & 0xFF, C2 & 0xFF);
-#pragma unroll
-        for (int s = 1; s < 32; s <<= 1) {
-            const uint32_t o = __shfl_down_sync(FULL, m, s);
-            if (lane + s < 32) m = compose(m, o);
-        }
-        uint32_t ex = __shfl_down_sync(FULL, m, 1);
-        if (lane == 31) ex = map_pack(0, 255);
-        const uint32_t h = S.J[y * PW + WR] & 0xFF;  // pixel x = BW of this row (halo)
-        const uint32_t vin = min(ex >> 8, max(ex & 0xFF, h));
-        const uint32_t r = vmin(C2, vmax(A2, vin * 0x01010101u));
-        const bool ch = (r != j);
-        if (ch) S.J[y * PW + w] = r;
-        const unsigned nch = __reduce_add_sync(FULL, (unsigned)__popc(__vcmpne4(r, j)) >> 3);
-        if (nch) {
-            any += nch;
-            if (lane == 0) atomicOr(&S.rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
-        }
-    }
-    return any;   // pixels changed (warp-uniform)
+    return scan_rows<CONN, false>(S.J, S.I, S.rowmask, r0, r1);
 }
 
 // One raster + anti-raster pair over the whole block; `bands` warps each take a
@@ -482,17 +523,32 @@ __device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp, bool changed_rows_only
             }
             if (!act) continue;
         }
+        // one geodesic dilation step in the two-plane form (see scan_rows)
         const uint32_t *rw = &S.J[y * PW];
         const uint32_t c = rw[w];
-        uint32_t m = vmax(c, vmax(west(rw[w - 1], c), east(c, rw[w + 1])));
+        const uint32_t cE = even_plane(c), cO = odd_plane(c);
+        // maxima over pixels x-1, x, x+1 of one row, for the even and the odd pixels
+        auto hmax = [](const uint32_t *row, int ww, uint32_t &hE, uint32_t &hO) {
+            const uint32_t v = row[ww], vE = even_plane(v), vO = odd_plane(v);
+            hE = __vimax3_u16x2(vE, __funnelshift_l(odd_plane(row[ww - 1]), vO, 16), vO);
+            hO = __vimax3_u16x2(vO, vE, __funnelshift_r(vE, even_plane(row[ww + 1]), 16));
+        };
+        uint32_t mE, mO;
+        hmax(rw, w, mE, mO);
         const uint32_t *up = rw - PW, *dn = rw + PW;
-        const uint32_t u = up[w], d = dn[w];
-        m = vmax(m, vmax(u, d));
         if (CONN == 8) {
-            m = vmax(m, vmax(west(up[w - 1], u), east(u, up[w + 1])));
-            m = vmax(m, vmax(west(dn[w - 1], d), east(d, dn[w + 1])));
+            uint32_t uE, uO, dE, dO;
+            hmax(up, w, uE, uO);
+            hmax(dn, w, dE, dO);
+            mE = __vimax3_u16x2(mE, uE, dE);
+            mO = __vimax3_u16x2(mO, uO, dO);
+        } else {
+            const uint32_t u = up[w], d = dn[w];
+            mE = __vimax3_u16x2(mE, even_plane(u), even_plane(d));
+            mO = __vimax3_u16x2(mO, odd_plane(u), odd_plane(d));
         }
-        const uint32_t nv = vmin(S.I[y * PW + w], m);
+        const uint32_t iw = S.I[y * PW + w];
+        const uint32_t nv = merge_planes(pmin(even_plane(iw), mE), pmin(odd_plane(iw), mO));
         const uint32_t diff = nv ^ c;
         if (diff) S.J[y * PW + w] = nv;
         if (__any_sync(FULL, diff != 0) && lane == 0)
