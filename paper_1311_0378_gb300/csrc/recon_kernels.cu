@@ -51,6 +51,8 @@ struct Smem {
     unsigned item, tile, flag, overflow, notify, visited;
     unsigned phase;               // parity of the TMA barrier's next completion
     unsigned abrt;                // block-uniform copy of the abort word
+    Work acc;                     // thread 0: counters of consecutive visits to tile acc_tile
+    int acc_tile;
 };
 
 __device__ __forceinline__ int find_tile(const Params &P, unsigned b)
@@ -948,15 +950,18 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
     // a visited block sits at its fixed point for the halo it last saw
     bool frame_only = visited;
     constexpr int MAX_SCAN_PAIRS = 1 << 16, MAX_RERUNS = 1 << 14, MAX_OVERFLOWS = 1 << 12, MAX_ADAPTIVE = 64;
-    if (visited && k >= 0 && (P.revisit_scans > 0 || D.gain > 0)) {
-        // revisit: fixed scan pairs, then more while a pair still raises at
-        // least scan_gain pixels (the tuned scan-to-queue switch, Sec. VI-B)
+    constexpr int REVISIT_SCAN_MIN = 64;   // frame pixels raised before a revisit turns to scans
+    // A revisit seeds from its frame first; only when that raised many frame
+    // pixels (a wide change arrived through the halo) does it switch to scan
+    // pairs -- fixed ones, then more while a pair still raises at least gain
+    // pixels (the tuned scan-to-queue switch, Sec. VI-B) -- and seed the whole block.
+    const bool scan_on_revisit = k >= 0 && (P.revisit_scans > 0 || D.gain > 0);
+    auto revisit_scans = [&]() {
         for (int s = 0; s < MAX_ADAPTIVE; ++s) {
             const unsigned g = scan_pair<BH, CONN>(S, P.bands, wk.scan_rows);
             if (g == 0 || (s + 1 >= P.revisit_scans && (D.gain == 0 || g < (unsigned)D.gain))) break;
         }
-        frame_only = false;   // the scans moved interior pixels: seed from the whole block
-    }
+    };
     if (!visited || k < 0) {
         const int pairs = k < 0 ? MAX_SCAN_PAIRS : k;
         int s = 0;
@@ -977,7 +982,16 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
             return true;
         }
         if (need_seed) {
-            unsigned n = frame_only ? seed_frame<BH, CONN>(S, gsp) : seed_pass<BH, CONN>(S, gsp);
+            unsigned n;
+            if (frame_only) {
+                n = seed_frame<BH, CONN>(S, gsp);
+                if (scan_on_revisit && n >= (unsigned)REVISIT_SCAN_MIN) {
+                    revisit_scans();
+                    n = seed_pass<BH, CONN>(S, gsp);
+                }
+            } else {
+                n = seed_pass<BH, CONN>(S, gsp);
+            }
             wk.seeds += 1;
             trace(P, 4, b);
             clk.tick(wk, PH_SEED);
@@ -1000,15 +1014,19 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
         __threadfence();
         edge_notify_bits<BH, CONN>(S);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 8) {   // one lane of warp 0 per direction, concurrently
             const unsigned bits = S.notify;
-            const int dys[8] = {-1, 1, 0, 0, -1, -1, 1, 1}, dxs[8] = {0, 0, -1, 1, -1, 1, -1, 1};
-            for (int d = 0; d < 8; ++d)
-                if (bits & (1u << d)) {
-                    const int ny = by + dys[d], nx = bx + dxs[d];
-                    if (ny >= 0 && ny < D.nby && nx >= 0 && nx < D.nbx)
-                        notify_block(P, D.block_base + (unsigned)(ny * D.nbx + nx));
-                }
+            const int d = threadIdx.x;
+            const int dy = (d == 0 || d == 4 || d == 5) ? -1 : ((d == 1 || d == 6 || d == 7) ? 1 : 0);
+            const int dx = (d == 2 || d == 4 || d == 6) ? -1 : ((d == 3 || d == 5 || d == 7) ? 1 : 0);
+            if (bits & (1u << d)) {
+                const int ny = by + dy, nx = bx + dx;
+                if (ny >= 0 && ny < D.nby && nx >= 0 && nx < D.nbx)
+                    notify_block(P, D.block_base + (unsigned)(ny * D.nbx + nx));
+            }
+        }
+        __syncwarp();
+        if (threadIdx.x == 0) {
             // let go of the block unless a neighbour changed our halo meanwhile
             const unsigned prev = atomicCAS(&P.state[b], S_RUN | S_VIS, S_IDLE | S_VIS);
             S.flag = (prev == (S_RUN | S_VIS)) ? 0u : 1u;
@@ -1040,20 +1058,13 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
         } else {
             need_seed = true;
             frame_only = true;
-            if (P.revisit_scans > 0 || D.gain > 0) {
-                for (int s2 = 0; s2 < MAX_ADAPTIVE; ++s2) {
-                    const unsigned g = scan_pair<BH, CONN>(S, P.bands, wk.scan_rows);
-                    if (g == 0 || (s2 + 1 >= P.revisit_scans && (D.gain == 0 || g < (unsigned)D.gain))) break;
-                }
-                frame_only = false;
-            }
         }
         clk.tick(wk, PH_SCAN);
     }
 }
 
 template <int BH>
-__global__ void __launch_bounds__(NT, 6) recon_persistent(Params P)
+__global__ void __launch_bounds__(NT, BH == 128 ? 4 : 6) recon_persistent(Params P)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<BH> &S = *reinterpret_cast<Smem<BH> *>(smem_raw);
@@ -1064,6 +1075,27 @@ __global__ void __launch_bounds__(NT, 6) recon_persistent(Params P)
         S.phase = 0;
     }
     __syncthreads();
+    // thread 0 accumulates the work counters of consecutive visits to one tile
+    // and publishes them when the CTA moves to another tile or leaves
+    Work &acc = S.acc;
+    int &acc_tile = S.acc_tile;
+    if (threadIdx.x == 0) {
+        acc = Work{0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}};
+        acc_tile = -1;
+    }
+    auto flush = [&]() {
+        if (threadIdx.x != 0 || acc_tile < 0) return;
+        Work &g = P.work[acc_tile];
+        atomicAdd(&g.visits, acc.visits);
+        if (acc.scan_rows) atomicAdd(&g.scan_rows, acc.scan_rows);
+        if (acc.pops) atomicAdd(&g.pops, acc.pops);
+        if (acc.seeds) atomicAdd(&g.seeds, acc.seeds);
+        if (acc.levels) atomicAdd(&g.levels, acc.levels);
+        atomicAdd(&g.busy_ns, acc.busy_ns);
+        for (int ph = 0; ph < NPH; ++ph)
+            if (acc.phase_ns[ph]) atomicAdd(&g.phase_ns[ph], acc.phase_ns[ph]);
+        acc = Work{0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}};
+    };
     for (;;) {
         const unsigned long long t_fetch = threadIdx.x == 0 ? gtimer() : 0ull;
         if (threadIdx.x == 0) {
@@ -1080,6 +1112,7 @@ __global__ void __launch_bounds__(NT, 6) recon_persistent(Params P)
         __syncthreads();
         const unsigned b = S.item;
         if (b == EMPTY) {
+            flush();
             trace(P, 15, 0);
             return;
         }
@@ -1100,14 +1133,17 @@ __global__ void __launch_bounds__(NT, 6) recon_persistent(Params P)
         if (threadIdx.x == 0) {
             // failed tile: drop the block without touching its pixels
             if (!released) atomicExch(&P.state[b], S_IDLE | S_VIS);
-            atomicAdd(&P.work[t].visits, wk.visits);
-            atomicAdd(&P.work[t].scan_rows, wk.scan_rows);
-            atomicAdd(&P.work[t].pops, wk.pops);
-            atomicAdd(&P.work[t].seeds, wk.seeds);
-            atomicAdd(&P.work[t].levels, wk.levels);
-            atomicAdd(&P.work[t].busy_ns, gtimer() - t_start);
-            for (int ph = 0; ph < NPH; ++ph)
-                if (wk.phase_ns[ph]) atomicAdd(&P.work[t].phase_ns[ph], wk.phase_ns[ph]);
+            if (t != acc_tile) {
+                flush();
+                acc_tile = t;
+            }
+            acc.visits += wk.visits;
+            acc.scan_rows += wk.scan_rows;
+            acc.pops += wk.pops;
+            acc.seeds += wk.seeds;
+            acc.levels += wk.levels;
+            acc.busy_ns += gtimer() - t_start;
+            for (int ph = 0; ph < NPH; ++ph) acc.phase_ns[ph] += wk.phase_ns[ph];
             __threadfence();
             atomicSub(&P.ctl->outstanding, 1u);
         }
