@@ -706,17 +706,6 @@ __device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t 
     return raised;
 }
 
-// Warp-inclusive prefix sum of c.
-__device__ __forceinline__ unsigned warp_incl(unsigned c)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned t = __shfl_up_sync(FULL, c, d);
-        if (lane >= d) c += t;
-    }
-    return c;
-}
 
 // Processes the wavefront level by level until it is empty (Algorithm 1's
 // propagation phase). Level L reads queue L % 2 and appends to (L + 1) % 2;
@@ -773,15 +762,22 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
                 const uint32_t v = act ? Jb[p] : 0u;
                 __syncwarp();
                 const unsigned raised = expand<CONN>(S.J, Jb, Ib, p, v, act, rows);
-                const unsigned c = __popc(raised);
-                const unsigned incl = warp_incl(c);
-                const unsigned tot = __shfl_sync(FULL, incl, 31);
-                if (tail + tot - (head + m) <= (unsigned)RING) {
-                    unsigned o = tail + incl - c;
+                // slots by direction: one ballot per neighbour direction, no prefix-sum chain
+                unsigned bal[CONN], tot = 0;
 #pragma unroll
-                    for (int k = 0; k < CONN; ++k)
+                for (int k = 0; k < CONN; ++k) {
+                    bal[k] = __ballot_sync(FULL, (raised >> k) & 1u);
+                    tot += __popc(bal[k]);
+                }
+                if (tail + tot - (head + m) <= (unsigned)RING) {
+                    const unsigned lt = lanemask_lt();
+                    unsigned o = tail;
+#pragma unroll
+                    for (int k = 0; k < CONN; ++k) {
                         if ((raised >> k) & 1u)
-                            ring[(o++) & (RING - 1)] = (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k]));
+                            ring[(o + __popc(bal[k] & lt)) & (RING - 1)] = (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k]));
+                        o += __popc(bal[k]);
+                    }
                     tail += tot;
                 } else if (lane == 0) {
                     S.overflow = 1;
@@ -806,18 +802,24 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
             const unsigned p = act ? get_entry(S, gsp, src, i) : safe_p;
             const uint32_t v = act ? Jb[p] : 0u;
             const unsigned raised = expand<CONN>(S.J, Jb, Ib, p, v, act, rows);
-            const unsigned c = __popc(raised);
-            const unsigned incl = warp_incl(c);
-            const unsigned tot = __shfl_sync(FULL, incl, 31);
+            unsigned bal[CONN], tot = 0;
+#pragma unroll
+            for (int k = 0; k < CONN; ++k) {
+                bal[k] = __ballot_sync(FULL, (raised >> k) & 1u);
+                tot += __popc(bal[k]);
+            }
             unsigned b0 = 0;
             if (tot) {
-                if (lane == 31) b0 = atomicAdd(&S.cq[cnext], tot);
-                b0 = __shfl_sync(FULL, b0, 31);
+                if (lane == 0) b0 = atomicAdd(&S.cq[cnext], tot);
+                b0 = __shfl_sync(FULL, b0, 0);
             }
-            unsigned o = b0 + incl - c;
+            const unsigned lt = lanemask_lt();
 #pragma unroll
-            for (int k = 0; k < CONN; ++k)
-                if ((raised >> k) & 1u) put_entry(S, gsp, dst, o++, (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k])));
+            for (int k = 0; k < CONN; ++k) {
+                if ((raised >> k) & 1u)
+                    put_entry(S, gsp, dst, b0 + __popc(bal[k] & lt), (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k])));
+                b0 += __popc(bal[k]);
+            }
         }
         __syncthreads();
         n = S.cq[cnext];
