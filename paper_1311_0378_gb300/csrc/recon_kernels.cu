@@ -46,7 +46,8 @@ struct Smem {
     uint8_t hIt[BW + 2], hIb[BW + 2];  // halo mask, top / bottom rows, x = -1 .. BW
     uint8_t hIl[BH], hIr[BH];          // halo mask, left / right columns
     uint8_t eT[BW], eB[BW], eL[BH], eR[BH];  // edge values when neighbours last saw them
-    unsigned rowmask[BH / 32];
+    unsigned rowmask[BH / 32];    // rows changed since the block was loaded
+    unsigned pairmask[BH / 32];   // rows changed by the latest scan pair
     unsigned cq[3];               // level sizes, rotating by level (see run_queue)
     unsigned item, tile, flag, overflow, notify, visited;
     unsigned phase;               // parity of the TMA barrier's next completion
@@ -346,7 +347,8 @@ __device__ __forceinline__ uint32_t compose(uint32_t g, uint32_t f)
 // broadcast load), and the next row's mask and marker words are loaded while
 // the current row is computed.
 template <int CONN, bool DOWN>
-__device__ __forceinline__ unsigned scan_rows(uint32_t *SJ, const uint32_t *SI, unsigned *rowmask, int r0, int r1)
+__device__ __forceinline__ unsigned scan_rows(uint32_t *SJ, const uint32_t *SI, unsigned *rowmask,
+                                              unsigned *pairmask, int r0, int r1)
 {
     const int lane = threadIdx.x & 31, w = lane + W0;
     const int step = DOWN ? 1 : -1;
@@ -418,7 +420,10 @@ __device__ __forceinline__ unsigned scan_rows(uint32_t *SJ, const uint32_t *SI, 
         const unsigned nch = __reduce_add_sync(FULL, nd);
         if (nch) {
             any += nch;
-            if (lane == 0) atomicOr(&rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
+            if (lane == 0) {
+                atomicOr(&rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
+                atomicOr(&pairmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
+            }
         }
         pE = rE;
         pO = rO;
@@ -432,13 +437,13 @@ __device__ __forceinline__ unsigned scan_rows(uint32_t *SJ, const uint32_t *SI, 
 template <int BH, int CONN>
 __device__ unsigned raster_rows(Smem<BH> &S, int r0, int r1)
 {
-    return scan_rows<CONN, true>(S.J, S.I, S.rowmask, r0, r1);
+    return scan_rows<CONN, true>(S.J, S.I, S.rowmask, S.pairmask, r0, r1);
 }
 
 template <int BH, int CONN>
 __device__ unsigned antiraster_rows(Smem<BH> &S, int r0, int r1)
 {
-    return scan_rows<CONN, false>(S.J, S.I, S.rowmask, r0, r1);
+    return scan_rows<CONN, false>(S.J, S.I, S.rowmask, S.pairmask, r0, r1);
 }
 
 // One raster + anti-raster pair over the whole block; `bands` warps each take a
@@ -449,6 +454,7 @@ __device__ unsigned scan_pair(Smem<BH> &S, int bands, unsigned long long &rows)
     // returns the number of pixels the pair changed (block-uniform)
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) S.flag = 0;
+    for (int i = threadIdx.x; i < BH / 32; i += NT) S.pairmask[i] = 0;
     __syncthreads();
     unsigned ch = 0;
     if (warp < bands) {
@@ -504,19 +510,21 @@ __device__ __forceinline__ void warp_push(Smem<BH> &S, uint16_t *gsp, int lvl, b
 // Seeding pass: J(p) <- max(J(p), min(I(p), max over N(p) of J)) in place;
 // every raised pixel joins level 0. Returns the level's size.
 template <int BH, int CONN>
-__device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp, bool changed_rows_only = false)
+__device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp, const unsigned *filter = nullptr)
 {
-    // changed_rows_only: just the rows changed since the load and their
-    // neighbours (the verification after an atomic-free queue phase)
+    // filter (optional): visit only rows within one row of a row set in it.
+    // After a scan pair every pixel has taken all eight directions into
+    // account, so only pixels next to a pixel that pair changed can still be
+    // raised: filter = the pair's changed rows.
     unsigned rm[BH / 32];
 #pragma unroll
-    for (int i = 0; i < BH / 32; ++i) rm[i] = S.rowmask[i];
+    for (int i = 0; i < BH / 32; ++i) rm[i] = filter ? filter[i] : 0u;
     __syncthreads();
     if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = lane + W0;
     for (int y = 1 + (threadIdx.x >> 5); y <= BH; y += NT / 32) {
-        if (changed_rows_only) {
+        if (filter) {
             bool act = false;
 #pragma unroll
             for (int d = -1; d <= 1; ++d) {
@@ -964,9 +972,11 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
             if (g == 0 || (s + 1 >= P.revisit_scans && (D.gain == 0 || g < (unsigned)D.gain))) break;
         }
     };
+    bool scanned = false;   // a scan pair ran this visit (its changed rows bound the seeding)
     if (!visited || k < 0) {
         const int pairs = k < 0 ? MAX_SCAN_PAIRS : k;
         int s = 0;
+        scanned = pairs > 0;
         for (; s < pairs; ++s) {
             if (!scan_pair<BH, CONN>(S, P.bands, wk.scan_rows)) { if (k < 0) need_seed = false; break; }
         }
@@ -989,10 +999,10 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
                 n = seed_frame<BH, CONN>(S, gsp);
                 if (scan_on_revisit && n >= (unsigned)REVISIT_SCAN_MIN) {
                     revisit_scans();
-                    n = seed_pass<BH, CONN>(S, gsp);
+                    n = seed_pass<BH, CONN>(S, gsp, S.pairmask);
                 }
             } else {
-                n = seed_pass<BH, CONN>(S, gsp);
+                n = seed_pass<BH, CONN>(S, gsp, scanned ? S.pairmask : nullptr);
             }
             wk.seeds += 1;
             trace(P, 4, b);
