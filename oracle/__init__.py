@@ -7,7 +7,10 @@ plain C (``recon_oracle.c``) plus NumPy for the cost model (``mlp.py``).
 Functions follow the definition of reconstruction by dilation (Table II,
 "Morphological Reconstruction", after Vincent 1993): R = lim delta_I^n(J) with
 delta_I(X)(p) = min(max_{q in N(p)} X(q), I(p)), N(p) the closed 4- or
-8-neighbourhood inside the image.
+8-neighbourhood inside the image. ``recon_erode`` is the dual (max and min
+exchanged, J >= I), and ``fill_holes`` is Table II's FillHoles: a flood of the
+background from the image border, written as complement -> reconstruction by
+dilation from the border -> complement.
 """
 from __future__ import annotations
 
@@ -51,7 +54,11 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
-        for f in (L.oracle_recon, L.oracle_recon_widest, L.oracle_dilate_step, L.oracle_recon_tiles):
+        L.oracle_recon_erode.argtypes = [u8p, u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]
+        L.oracle_erode_step.argtypes = [u8p, u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        for f in (L.oracle_recon, L.oracle_recon_widest, L.oracle_dilate_step, L.oracle_recon_tiles,
+                  L.oracle_recon_erode, L.oracle_erode_step):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -97,11 +104,50 @@ def dilate_step(I: np.ndarray, X: np.ndarray, conn: int = 8) -> Tuple[np.ndarray
     return Y, bool(rc)
 
 
+def recon_erode(I: np.ndarray, J: np.ndarray, conn: int = 8, return_pairs: bool = False):
+    """Reconstruction by erosion: R = lim eps_I^n(J), eps_I(X)(p) =
+    max(min_{q in N(p)} X(q), I(p)), by raster / anti-raster sweeps until a
+    full pair changes nothing. Requires J >= I (ValueError, status 2,
+    otherwise). Returns R; J is not modified."""
+    I, R = _prep(I, J)
+    pairs = ctypes.c_int(0)
+    rc = lib().oracle_recon_erode(I.ctypes.data, R.ctypes.data, I.shape[0], I.shape[1], conn,
+                                  ctypes.byref(pairs))
+    if rc != OK:
+        raise ValueError("oracle_recon_erode status %d" % rc)
+    return (R, pairs.value) if return_pairs else R
+
+
+def erode_step(I: np.ndarray, X: np.ndarray, conn: int = 8) -> Tuple[np.ndarray, bool]:
+    """One whole-image geodesic erosion max(eps(X), I); returns (new X, changed)."""
+    I, Y = _prep(I, X)
+    rc = lib().oracle_erode_step(I.ctypes.data, Y.ctypes.data, I.shape[0], I.shape[1], conn)
+    if rc < 0:
+        raise ValueError("oracle_erode_step status %d" % -rc)
+    return Y, bool(rc)
+
+
+def fill_holes(I: np.ndarray, conn: int = 8) -> np.ndarray:
+    """FillHoles (Table II): flood the background from the image border and
+    raise every pixel the flood cannot reach (a hole) to the lowest level that
+    encloses it. Definition used: C = 255 - I; marker M = C on the one-pixel
+    image border, 0 inside; result = 255 - R^delta_C(M), with R^delta the
+    reconstruction by dilation of ``recon``."""
+    I = np.ascontiguousarray(I, dtype=np.uint8)
+    if I.ndim != 2:
+        raise ValueError("I must be a 2-D array")
+    C = (255 - I.astype(np.int16)).astype(np.uint8)
+    M = np.zeros_like(C)
+    M[0, :], M[-1, :], M[:, 0], M[:, -1] = C[0, :], C[-1, :], C[:, 0], C[:, -1]
+    return (255 - recon(C, M, conn).astype(np.int16)).astype(np.uint8)
+
+
 def recon_tiles(pairs: Sequence[Tuple[np.ndarray, np.ndarray]], conns: Sequence[int],
                 method: str = "sweep", nthreads: int = 0) -> Tuple[List[np.ndarray], int]:
     """Reconstructs independent tiles on host threads (0 = all cores).
 
-    Returns ([R_t], threads used). method is "sweep" or "widest"."""
+    Returns ([R_t], threads used). method is "sweep" or "widest" (reconstruction
+    by dilation) or "erode" (reconstruction by erosion, J >= I)."""
     n = len(pairs)
     Is, Rs = [], []
     for I, J in pairs:
@@ -115,7 +161,8 @@ def recon_tiles(pairs: Sequence[Tuple[np.ndarray, np.ndarray]], conns: Sequence[
     Cs = (ctypes.c_int * max(n, 1))(*conns)
     st = (ctypes.c_int * max(n, 1))()
     nt = nthreads or (os.cpu_count() or 1)
-    used = lib().oracle_recon_tiles(n, Ip, Rp, Hs, Ws, Cs, 1 if method == "widest" else 0, nt, st)
+    code = {"sweep": 0, "widest": 1, "erode": 2}[method]
+    used = lib().oracle_recon_tiles(n, Ip, Rp, Hs, Ws, Cs, code, nt, st)
     bad = [i for i in range(n) if st[i] != OK]
     if bad:
         raise ValueError("oracle tiles failed: %s" % [(i, st[i]) for i in bad[:5]])

@@ -18,6 +18,14 @@
  *                        min(J(q), min of I on the path), computed as a
  *                        maximum-bottleneck (widest-path) flood that finalises
  *                        pixels in decreasing value order with 256 buckets.
+ * oracle_recon_erode -- reconstruction by erosion, the dual operation:
+ *                        R = lim_n eps_I^n(J), eps_I(X)(p) = max( min_{q in N(p)} X(q), I(p) ),
+ *                        precondition J >= I. Written out with min and max
+ *                        exchanged (absent neighbours are skipped, as above), not
+ *                        through complements, so the duality
+ *                        R^eps_I(J) = 255 - R^delta_{255-I}(255-J) tests it.
+ *                        It is what FillHoles (Table II) computes when the marker
+ *                        is I on the image border and 255 inside.
  * Both are single-threaded per tile; oracle_recon_tiles runs tiles on threads.
  */
 #include <pthread.h>
@@ -132,6 +140,104 @@ int oracle_dilate_step(const uint8_t *I, uint8_t *X, int H, int W, int conn)
     return changed;
 }
 
+/* ---- reconstruction by erosion ---- */
+
+static int check_erode(const uint8_t *I, const uint8_t *J, int H, int W, int conn)
+{
+    if (!I || !J || H <= 0 || W <= 0 || (conn != 4 && conn != 8)) return ORACLE_EINVAL;
+    size_t n = (size_t)H * (size_t)W;
+    for (size_t i = 0; i < n; ++i)
+        if (J[i] < I[i]) return ORACLE_EMARKER;
+    return ORACLE_OK;
+}
+
+/* Raster scan of the erosion: J(p) <- max(I(p), min(J(p), J over N+(p))). */
+static int raster_erode(const uint8_t *I, uint8_t *J, int H, int W, int conn)
+{
+    int changed = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            uint8_t m = J[p];
+            if (x > 0) m = u8min(m, J[p - 1]);
+            if (y > 0) {
+                m = u8min(m, J[p - W]);
+                if (conn == 8) {
+                    if (x > 0) m = u8min(m, J[p - W - 1]);
+                    if (x < W - 1) m = u8min(m, J[p - W + 1]);
+                }
+            }
+            uint8_t v = u8max(m, I[p]);
+            if (v != J[p]) { J[p] = v; changed = 1; }
+        }
+    return changed;
+}
+
+/* Anti-raster scan of the erosion, with the mirrored set N-(p). */
+static int antiraster_erode(const uint8_t *I, uint8_t *J, int H, int W, int conn)
+{
+    int changed = 0;
+    for (int y = H - 1; y >= 0; --y)
+        for (int x = W - 1; x >= 0; --x) {
+            size_t p = (size_t)y * W + x;
+            uint8_t m = J[p];
+            if (x < W - 1) m = u8min(m, J[p + 1]);
+            if (y < H - 1) {
+                m = u8min(m, J[p + W]);
+                if (conn == 8) {
+                    if (x < W - 1) m = u8min(m, J[p + W + 1]);
+                    if (x > 0) m = u8min(m, J[p + W - 1]);
+                }
+            }
+            uint8_t v = u8max(m, I[p]);
+            if (v != J[p]) { J[p] = v; changed = 1; }
+        }
+    return changed;
+}
+
+/* Erosion sweeps to stability (J >= I required, else status 2). */
+int oracle_recon_erode(const uint8_t *I, uint8_t *J, int H, int W, int conn, int *pairs)
+{
+    int rc = check_erode(I, J, H, W, conn);
+    if (rc) return rc;
+    int n = 0;
+    for (;;) {
+        int c1 = raster_erode(I, J, H, W, conn);
+        int c2 = antiraster_erode(I, J, H, W, conn);
+        ++n;
+        if (!c1 && !c2) break;
+    }
+    if (pairs) *pairs = n;
+    return ORACLE_OK;
+}
+
+/* One whole-image geodesic erosion X <- max(eps(X), I), every pixel reading
+ * the old X. Returns 1 if any pixel changed. */
+int oracle_erode_step(const uint8_t *I, uint8_t *X, int H, int W, int conn)
+{
+    if (!I || !X || H <= 0 || W <= 0 || (conn != 4 && conn != 8)) return -ORACLE_EINVAL;
+    size_t n = (size_t)H * (size_t)W;
+    uint8_t *old = (uint8_t *)malloc(n);
+    if (!old) return -ORACLE_ENOMEM;
+    memcpy(old, X, n);
+    int changed = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            uint8_t m = 255;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (conn == 4 && dy != 0 && dx != 0) continue;
+                    int yy = y + dy, xx = x + dx;
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    m = u8min(m, old[(size_t)yy * W + xx]);
+                }
+            uint8_t v = u8max(m, I[(size_t)y * W + x]);
+            if (v != X[(size_t)y * W + x]) { X[(size_t)y * W + x] = v; changed = 1; }
+        }
+    free(old);
+    return changed;
+}
+
 /* ---- maximum-bottleneck flood (test cross-check / large inputs) ---- */
 typedef struct { uint32_t *v; size_t n, cap; } bucket_t;
 
@@ -204,13 +310,15 @@ static void *tworker(void *arg)
         pthread_mutex_unlock(&t->mu);
         if (i >= t->n) break;
         int rc = t->method == 1 ? oracle_recon_widest(t->I[i], t->J[i], t->H[i], t->W[i], t->conn[i])
+               : t->method == 2 ? oracle_recon_erode(t->I[i], t->J[i], t->H[i], t->W[i], t->conn[i], NULL)
                                 : oracle_recon(t->I[i], t->J[i], t->H[i], t->W[i], t->conn[i], NULL);
         if (t->status) t->status[i] = rc;
     }
     return NULL;
 }
 
-/* Runs n independent tiles. method 0 = sweeps to stability, 1 = widest flood.
+/* Runs n independent tiles. method 0 = sweeps to stability, 1 = widest flood,
+ * 2 = erosion sweeps to stability.
  * status[i] (optional) receives each tile's code. Returns the number of threads used. */
 int oracle_recon_tiles(int n, const uint8_t *const *I, uint8_t *const *J, const int *H,
                        const int *W, const int *conn, int method, int nthreads, int *status)
