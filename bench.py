@@ -8,6 +8,12 @@ graph). Default workload "single4096": one 4096 x 4096 mask with 6711 blobs,
 reconstructed four times per step (4- and 8-connectivity x h-dome and
 fill-holes markers) as one 4-tile batch. Metric: reconstructed Mpix/s.
 
+--op selects the operation: "dilate" (the default, reconstruction by
+dilation), "erode" (reconstruction by erosion of the complemented pairs, the
+same propagation work as the dilation tiles) or "fill_holes" (FillHoles of
+every distinct (mask, connectivity) of the workload; the output needs no
+reset, so a step is the library call alone).
+
 Timing: CUDA events on the library's stream around each step; L2 is flushed
 (a 512 MiB write) before every timed step, outside the events. Under torchrun
 each rank runs the same batch (tiles are independent: weak scaling) and the
@@ -28,7 +34,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
-ALG_BYTES_PER_PX = 3  # read I, read J, write R: compulsory traffic of one reconstruction
+# compulsory traffic per pixel: read I, read J, write R (reconstruction by
+# dilation or erosion); read I, write the result (FillHoles)
+ALG_BYTES_PER_PX = {"dilate": 3, "erode": 3, "fill_holes": 2}
+OP_CODE = {"dilate": 0, "erode": 1, "fill_holes": 2}
 
 
 def kernel_hash():
@@ -109,18 +118,29 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def workload_tiles(name):
+def workload_tiles(name, op="dilate"):
     import synth
-    if name == "single4096":
-        w = synth.workload("single4096")
-        return w, w.tiles, True
     w = synth.workload(name)
-    return w, w.tiles, False
+    tiles = w.tiles
+    if op == "fill_holes" and name == "single4096":
+        # one shared mask: the marker kinds collapse, one tile per connectivity
+        seen, tiles = set(), []
+        for t in w.tiles:
+            if t.conn not in seen:
+                seen.add(t.conn)
+                tiles.append(t)
+    return w, tiles, name == "single4096"
 
 
-def gen_host(w, tiles, shared_mask):
-    """Pinned host tensors: masks and pristine markers for every tile."""
-    import numpy as np
+def complement_(t):
+    """In place: v -> 255 - v (turns a dilation pair into an erosion pair)."""
+    t.bitwise_not_()
+    return t
+
+
+def gen_host(w, tiles, shared_mask, op="dilate"):
+    """Pinned host tensors: masks and pristine markers for every tile (for
+    erosion, the complemented pairs)."""
     import torch
     import synth
     if shared_mask:
@@ -128,24 +148,43 @@ def gen_host(w, tiles, shared_mask):
         I = torch.from_numpy(pairs[0][0]).pin_memory()
         Is = [I] * len(tiles)
         Js = [torch.from_numpy(J).pin_memory() for _, J in pairs]
-        return Is, Js
-    Is = [torch.empty((t.H, t.W), dtype=torch.uint8).pin_memory() for t in tiles]
-    Js = [torch.empty((t.H, t.W), dtype=torch.uint8).pin_memory() for t in tiles]
-    synth.generate_into(tiles, w.seed, [x.data_ptr() for x in Is], [x.data_ptr() for x in Js])
+    else:
+        Is = [torch.empty((t.H, t.W), dtype=torch.uint8).pin_memory() for t in tiles]
+        Js = [torch.empty((t.H, t.W), dtype=torch.uint8).pin_memory() for t in tiles]
+        synth.generate_into(tiles, w.seed, [x.data_ptr() for x in Is], [x.data_ptr() for x in Js])
+    if op == "erode":
+        for x in ({id(x): x for x in Is}.values()):
+            complement_(x)
+        for x in Js:
+            complement_(x)
     return Is, Js
 
 
-def cpu_baseline(w, tiles, shared_mask, budget_tiles=None):
-    """The CPU oracle (sweeps to stability), as it stands, on host threads."""
+def oracle_op(pairs, conns, op, nthreads):
+    """The CPU oracle for one operation over independent tiles on host
+    threads; erosion pairs come already complemented."""
     import oracle
+    if op == "fill_holes":
+        from concurrent.futures import ThreadPoolExecutor   # the C oracle releases the GIL
+        with ThreadPoolExecutor(max_workers=max(1, nthreads)) as ex:
+            list(ex.map(lambda a: oracle.fill_holes(a[0][0], a[1]), zip(pairs, conns)))
+        return max(1, min(nthreads, len(pairs)))
+    _, used = oracle.recon_tiles(pairs, conns, "erode" if op == "erode" else "sweep", nthreads=nthreads)
+    return used
+
+
+def cpu_baseline(w, tiles, shared_mask, budget_tiles=None, op="dilate"):
+    """The CPU oracle (sweeps to stability), as it stands, on host threads."""
     import synth
     sample = tiles if budget_tiles is None else tiles[:budget_tiles]
     pairs = synth.generate(sample, w.seed)
+    if op == "erode":   # input preparation, outside the timing
+        pairs = [(255 - I, 255 - J) for I, J in pairs]
     t0 = time.perf_counter()
-    _, used = oracle.recon_tiles(pairs, [t.conn for t in sample], "sweep", nthreads=len(sample))
+    used = oracle_op(pairs, [t.conn for t in sample], op, len(sample))
     dt = time.perf_counter() - t0
     px = sum(t.H * t.W for t in sample)
-    return px, dt, used, "%d of %d tiles (%s), full size" % (len(sample), len(tiles), w.name)
+    return px, dt, used, "%d of %d tiles (%s), full size, op %s" % (len(sample), len(tiles), w.name, op)
 
 
 def run_reference(args):
@@ -155,15 +194,22 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w, tiles, shared = workload_tiles(args.workload)
+    w, tiles, shared = workload_tiles(args.workload, args.op)
     # one step = one tile of the workload, rotating through the tiles, each
     # reconstructed in full by the oracle on one host thread
     pairs = synth.generate(tiles, w.seed) if len(tiles) <= 8 else None
     def step(i):
         t = tiles[i % len(tiles)]
         I, J = pairs[i % len(tiles)] if pairs else synth.tile_pair(t, w.seed)
+        if args.op == "erode":
+            I, J = 255 - I, 255 - J
         t0 = time.perf_counter()
-        oracle.recon(I, J, t.conn)
+        if args.op == "erode":
+            oracle.recon_erode(I, J, t.conn)
+        elif args.op == "fill_holes":
+            oracle.fill_holes(I, t.conn)
+        else:
+            oracle.recon(I, J, t.conn)
         return time.perf_counter() - t0, t.H * t.W
     for i in range(args.warmup):
         step(i)
@@ -177,7 +223,8 @@ def run_reference(args):
             "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1000 * tot_t / max(args.steps, 1), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": w.name, "step": "one tile per step, rotating", "conn": "per tile"},
+            "config": {"workload": w.name, "op": args.op, "step": "one tile per step, rotating",
+                       "conn": "per tile"},
             "cpu_baseline": {"value": round(v, 3), "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                              "sample": "one full tile per step, rotating through the %d tiles" % len(tiles)},
             "e2e": {"value": round(v, 3), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -258,6 +305,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="single4096",
                     choices=["single4096", "single512", "batch64", "uneven1000"])
+    ap.add_argument("--op", default="dilate", choices=sorted(OP_CODE),
+                    help="dilate: reconstruction by dilation; erode: by erosion (complemented pairs); "
+                         "fill_holes: FillHoles of the masks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--block-h", type=int, default=0)
@@ -291,8 +341,10 @@ def main():
     if dist:
         dist.barrier()
 
-    w, tiles, shared = workload_tiles(args.workload)
-    Is_h, Js_h = gen_host(w, tiles, shared)
+    w, tiles, shared = workload_tiles(args.workload, args.op)
+    Is_h, Js_h = gen_host(w, tiles, shared, args.op)
+    opc = OP_CODE[args.op]
+    reset_j = args.op != "fill_holes"   # a FillHoles output needs no reset
     dev = torch.device("cuda", local)
     if shared:
         Id = Is_h[0].to(dev)
@@ -315,7 +367,7 @@ def main():
             rc.check(rc.recon_set_param(ctx, key, val))
     if args.sweeps != -99:
         rc.check(rc.recon_set_param(ctx, rc.RECON_P_SWEEPS, args.sweeps))
-    desc = [(I.data_ptr(), J.data_ptr(), t.H, t.W, t.W, t.conn) for I, J, t in zip(Is, Js, tiles)]
+    desc = [(I.data_ptr(), J.data_ptr(), t.H, t.W, t.W, t.conn, opc) for I, J, t in zip(Is, Js, tiles)]
     tuned = None
     if args.autotune:
         st, tuned = rc.recon_autotune(ctx, desc, 2)
@@ -331,9 +383,10 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def step():
-        with torch.cuda.stream(stream):
-            for J, J0_ in zip(Js, J0):
-                J.copy_(J0_, non_blocking=True)
+        if reset_j:
+            with torch.cuda.stream(stream):
+                for J, J0_ in zip(Js, J0):
+                    J.copy_(J0_, non_blocking=True)
         st = rc.recon_batch(ctx, desc)
         if st != rc.RECON_OK:
             raise rc.ReconError(st, "recon_batch")
@@ -371,7 +424,7 @@ def main():
 
     # end to end: host (pinned) buffers through recon_batch_host
     Jh = [x.clone().pin_memory() for x in Js_h]
-    htiles = [(I.data_ptr(), J.data_ptr(), t.H, t.W, t.W, t.conn) for I, J, t in zip(Is_h, Jh, tiles)]
+    htiles = [(I.data_ptr(), J.data_ptr(), t.H, t.W, t.W, t.conn, opc) for I, J, t in zip(Is_h, Jh, tiles)]
     e2e_ms = []
     for i in range(args.e2e_steps + 1):
         for a, b in zip(Jh, Js_h):
@@ -383,7 +436,7 @@ def main():
         if i > 0:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e = world * px / (statistics.median(e2e_ms) / 1e3) / 1e6
-    h2d = sum(2 * t.H * t.W for t in tiles)
+    h2d = sum((2 if reset_j else 1) * t.H * t.W for t in tiles)
     d2h = px
     rc.recon_free(ctx)
 
@@ -393,28 +446,32 @@ def main():
         return 0
     pk, src = peaks()
     kms = statistics.mean(kern_ms)
-    achieved = ALG_BYTES_PER_PX * px / (kms / 1e3) / 1e9
+    alg = ALG_BYTES_PER_PX[args.op]
+    achieved = alg * px / (kms / 1e3) / 1e9
+    traffic_key = w.name if args.op == "dilate" else "%s:%s" % (w.name, args.op)
     line = {
         "metric": "reconstructed Mpix/s", "value": round(value, 2), "unit": "Mpix/s",
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": w.name, "tiles": len(tiles), "pixels_per_step": px,
-                   "conn": sorted({t.conn for t in tiles}), "markers": "h-dome + fill-holes",
+        "config": {"workload": w.name, "op": args.op, "tiles": len(tiles), "pixels_per_step": px,
+                   "conn": sorted({t.conn for t in tiles}),
+                   "markers": "h-dome + fill-holes" if reset_j else "border (FillHoles)",
                    "l2": "flushed before each timed step (512 MiB write)", "bit_exact": "see tests -m gpu",
                    **params},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": round(achieved / pk["hbm_gbs"], 5), "traffic": measured_traffic(w.name),
+                     "frac": round(achieved / pk["hbm_gbs"], 5), "traffic": measured_traffic(traffic_key),
                      "kernel": "recon_persistent", "kernel_ms": round(kms, 4),
-                     "alg_bytes_per_px": ALG_BYTES_PER_PX, "peak_source": src},
+                     "alg_bytes_per_px": alg, "peak_source": src},
         "e2e": {"value": round(e2e, 2), "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        # per step: init + persistent kernel, plus features, finalize and MLP forward when learned
-        "gpu_launches": (5 if learned else 2) * args.steps,
+        # per step: init + persistent kernel, plus features, finalize and MLP forward
+        # when learned, plus the marker kernel for FillHoles
+        "gpu_launches": ((5 if learned else 2) + (0 if reset_j else 1)) * args.steps,
         "compare": compare,
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
-        cpx, cdt, used, sample = cpu_baseline(w, tiles, shared, None if len(tiles) <= 8 else 4)
+        cpx, cdt, used, sample = cpu_baseline(w, tiles, shared, None if len(tiles) <= 8 else 4, args.op)
         line["cpu_baseline"] = {"value": round(cpx / cdt / 1e6, 3), "unit": "Mpix/s", "cores": used,
                                 "kind": "oracle", "sample": sample, "seconds": round(cdt, 2)}
     print(json.dumps(line), flush=True)

@@ -11,6 +11,19 @@
  * first, then queue-driven propagation. R is unique, so every schedule returns
  * the same bytes.
  *
+ * Two more operations run on the same engine (recon_tile.op):
+ *   reconstruction by erosion, the dual: R = lim_n eps_I^n(J),
+ *     eps_I(X)(p) = max( min_{q in N(p)} X(q), I(p) ), for J >= I;
+ *   FillHoles (Table II: fill the holes of image objects by a flood of the
+ *     background from selected points, here the image border): the erosion of
+ *     the marker "I on the one-pixel image border, 255 inside" under I, which
+ *     equals complement -> border-seeded reconstruction by dilation ->
+ *     complement. A pixel the border flood cannot reach is raised to the
+ *     lowest level that encloses it.
+ * Both are the dilation run on complemented values (255 - v): the kernels
+ * complement pixels as they load and store them, and treat pixels outside the
+ * image as absent, so no complemented copy of I or J is ever written.
+ *
  * Images are uint8, row-major, `pitch` bytes between rows (pitch >= W). All
  * image pointers handed to recon_run / recon_batch are DEVICE pointers owned by
  * the caller; J is read as the marker and overwritten in place with R (as D is
@@ -38,8 +51,9 @@ typedef struct recon_ctx recon_ctx;
 enum {
     RECON_OK = 0,
     RECON_EINVAL = 1,    /* bad argument (null pointer, size, conn not 4/8, pitch < W) */
-    RECON_EMARKER = 2,   /* J > I at some pixel: the precondition J <= I does not hold.
-                            J of that tile is then left in an unspecified state. */
+    RECON_EMARKER = 2,   /* the marker violates its operation's precondition at some
+                            pixel (dilation: J > I; erosion: J < I). J of that tile
+                            is then left in an unspecified state. */
     RECON_ENOMEM = 3,    /* device or host allocation failed */
     RECON_ECUDA = 4,     /* a CUDA runtime call failed */
     RECON_ETIMEOUT = 5   /* a bounded device-side wait ran out; outputs unspecified */
@@ -51,12 +65,21 @@ enum {
 #define RECON_FLAG_LEARNED   0x4u  /* recon_batch: the cost model picks variant and order */
 #define RECON_FLAG_NO_GRAPH  0x8u  /* recon_batch: never capture / replay a CUDA graph */
 
+/* Operations (recon_tile.op). */
+enum {
+    RECON_OP_DILATE = 0,     /* reconstruction by dilation (Table II), J <= I */
+    RECON_OP_ERODE = 1,      /* reconstruction by erosion (the dual), J >= I */
+    RECON_OP_FILL_HOLES = 2  /* FillHoles (Table II) of I; J's input is ignored and
+                                J receives the result */
+};
+
 /* One tile of a batch: device pointers, caller-owned. */
 typedef struct {
     const uint8_t *I;   /* mask, H x W, row stride `pitch` bytes */
     uint8_t *J;         /* marker in, R out (in place) */
     int H, W, pitch;    /* H, W >= 1; pitch >= W */
     int conn;           /* 4 or 8 */
+    int op;             /* RECON_OP_*; 0 (dilation) when zero-initialised */
 } recon_tile;
 
 /* Creates a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
@@ -67,6 +90,11 @@ int recon_init(recon_ctx **ctx, int device, void *cuda_stream, unsigned flags);
 /* Reconstructs one tile (Table II; Algorithm 1 with the hybrid scan + queue
  * schedule of Sec. VI-B). I, J: device pointers, pitch = W. J <- R in place. */
 int recon_run(recon_ctx *ctx, const uint8_t *I, uint8_t *J, int H, int W, int conn);
+
+/* recon_run for any operation: op = RECON_OP_DILATE, RECON_OP_ERODE (J >= I,
+ * J <- the reconstruction by erosion) or RECON_OP_FILL_HOLES (J <- FillHoles(I);
+ * J need not be initialised). Device pointers, pitch = W. */
+int recon_run_op(recon_ctx *ctx, const uint8_t *I, uint8_t *J, int H, int W, int conn, int op);
 
 /* Reconstructs n independent tiles of any sizes in one persistent launch
  * (tiles are processed concurrently, as the 4K x 4K tiles of Sec. V are).
@@ -90,7 +118,8 @@ int recon_batch_ex(recon_ctx *ctx, const recon_tile *tiles, int n, const int *va
  * Copies in, reconstructs, copies R back into J, and waits. */
 int recon_run_host(recon_ctx *ctx, const uint8_t *I, uint8_t *J, int H, int W, int conn);
 
-/* End-to-end batch: tiles[].I / tiles[].J are HOST pointers; waits. */
+/* End-to-end batch: tiles[].I / tiles[].J are HOST pointers; waits. The J of
+ * a FillHoles tile is only written. */
 int recon_batch_host(recon_ctx *ctx, const recon_tile *tiles, int n);
 
 /* Waits for the context's stream; returns the device status of the last call. */

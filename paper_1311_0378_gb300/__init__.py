@@ -22,9 +22,10 @@ RECON_FLAG_SYNC, RECON_FLAG_NO_CHECK, RECON_FLAG_LEARNED, RECON_FLAG_NO_GRAPH = 
 (RECON_P_BLOCK_H, RECON_P_SWEEPS, RECON_P_GRID, RECON_P_BANDS, RECON_P_WAIT_NS, RECON_P_ORDER,
  RECON_P_TEST_STALL, RECON_P_TMA, RECON_P_TRACE, RECON_P_LAST_ABORT, RECON_P_REVISIT_SCANS,
  RECON_P_SCAN_GAIN) = range(1, 13)
+RECON_OP_DILATE, RECON_OP_ERODE, RECON_OP_FILL_HOLES = 0, 1, 2
 
 # every symbol the header declares; tests check the library exports them all
-SYMBOLS = ("recon_init", "recon_run", "recon_batch", "recon_batch_ex", "recon_run_host",
+SYMBOLS = ("recon_init", "recon_run", "recon_run_op", "recon_batch", "recon_batch_ex", "recon_run_host",
            "recon_batch_host", "recon_sync", "recon_last_error_tile", "recon_free",
            "recon_strerror", "recon_set_param", "recon_get_param", "recon_get_work",
            "recon_last_kernel_ms", "recon_features", "recon_mlp_forward", "recon_mlp_grad",
@@ -35,7 +36,8 @@ RECON_NFEAT, RECON_MLP_NPARAMS = 20, 5634
 
 class recon_tile(ctypes.Structure):
     _fields_ = [("I", ctypes.c_void_p), ("J", ctypes.c_void_p), ("H", ctypes.c_int),
-                ("W", ctypes.c_int), ("pitch", ctypes.c_int), ("conn", ctypes.c_int)]
+                ("W", ctypes.c_int), ("pitch", ctypes.c_int), ("conn", ctypes.c_int),
+                ("op", ctypes.c_int)]
 
 
 class recon_work(ctypes.Structure):
@@ -68,6 +70,7 @@ def lib() -> ctypes.CDLL:
     sig = {
         "recon_init": ([ctypes.POINTER(vp), i, vp, u], i),
         "recon_run": ([vp, vp, vp, i, i, i], i),
+        "recon_run_op": ([vp, vp, vp, i, i, i, i], i),
         "recon_batch": ([vp, tp, i], i),
         "recon_batch_ex": ([vp, tp, i, ip, ip], i),
         "recon_run_host": ([vp, vp, vp, i, i, i], i),
@@ -100,10 +103,11 @@ def lib() -> ctypes.CDLL:
     return L
 
 
-def _tiles(tiles: Sequence[Tuple[int, int, int, int, int, int]]):
+def _tiles(tiles: Sequence[Tuple[int, ...]]):
+    """(I, J, H, W, pitch, conn) or (I, J, H, W, pitch, conn, op) per tile."""
     arr = (recon_tile * max(len(tiles), 1))()
-    for k, (I, J, H, W, pitch, conn) in enumerate(tiles):
-        arr[k] = recon_tile(I, J, H, W, pitch, conn)
+    for k, t in enumerate(tiles):
+        arr[k] = recon_tile(*t) if len(t) == 7 else recon_tile(*t, RECON_OP_DILATE)
     return arr
 
 
@@ -127,8 +131,12 @@ def recon_run(ctx, I: int, J: int, H: int, W: int, conn: int) -> int:
     return lib().recon_run(ctx, I, J, H, W, conn)
 
 
+def recon_run_op(ctx, I: int, J: int, H: int, W: int, conn: int, op: int) -> int:
+    return lib().recon_run_op(ctx, I, J, H, W, conn, op)
+
+
 def recon_batch(ctx, tiles) -> int:
-    """tiles: sequence of (I, J, H, W, pitch, conn) with device addresses."""
+    """tiles: sequence of (I, J, H, W, pitch, conn[, op]) with device addresses."""
     return lib().recon_batch(ctx, _tiles(tiles), len(tiles))
 
 
@@ -141,7 +149,7 @@ def recon_run_host(ctx, I: int, J: int, H: int, W: int, conn: int) -> int:
 
 
 def recon_batch_host(ctx, tiles) -> int:
-    """tiles: sequence of (I, J, H, W, pitch, conn) with HOST addresses."""
+    """tiles: sequence of (I, J, H, W, pitch, conn[, op]) with HOST addresses."""
     return lib().recon_batch_host(ctx, _tiles(tiles), len(tiles))
 
 

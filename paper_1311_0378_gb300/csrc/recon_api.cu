@@ -20,6 +20,7 @@ extern "C" size_t rk_smem_bytes(int bh);
 extern "C" cudaError_t rk_configure(int bh, int *ctas_per_sm);
 extern "C" cudaError_t rk_launch_init(int grid, const rk::Params *P, cudaStream_t st);
 extern "C" cudaError_t rk_launch_main(int bh, int grid, const rk::Params *P, cudaStream_t st);
+extern "C" cudaError_t rk_launch_fill(const rk::TileDesc *tiles, const int *list, int nlist, cudaStream_t st);
 
 struct recon_ctx {
     int device = 0;
@@ -165,6 +166,7 @@ static int tile_ok(const recon_tile &t)
 {
     if (!t.I || !t.J || t.H < 1 || t.W < 1 || t.pitch < t.W) return 0;
     if (t.conn != 4 && t.conn != 8) return 0;
+    if (t.op != RECON_OP_DILATE && t.op != RECON_OP_ERODE && t.op != RECON_OP_FILL_HOLES) return 0;
     if ((double)t.H * (double)t.pitch > 9.0e18) return 0;
     return 1;
 }
@@ -276,15 +278,17 @@ static int encode_map(CUtensorMap *m, const void *base, int H, int W, int pitch,
 }
 
 struct MetaLayout {
-    size_t off_order, off_base, off_maps, total;
+    size_t off_order, off_base, off_fill, off_maps, total;
 };
 
+// descriptors | packing order | block bases | FillHoles tile list | tensor maps
 static MetaLayout meta_layout(int n)
 {
     MetaLayout L;
     L.off_order = align_up(sizeof(rk::TileDesc) * n, 16);
     L.off_base = align_up(L.off_order + sizeof(int) * n, 16);
-    L.off_maps = align_up(L.off_base + sizeof(unsigned) * (n + 1), 128);
+    L.off_fill = align_up(L.off_base + sizeof(unsigned) * (n + 1), 16);
+    L.off_maps = align_up(L.off_fill + sizeof(int) * n, 128);
     L.total = L.off_maps + 256 * (size_t)n;
     return L;
 }
@@ -292,7 +296,7 @@ static MetaLayout meta_layout(int n)
 // Builds the descriptor table + packing tables in the pinned staging buffer.
 // Returns bytes used, or 0 on failure.
 static int stage_meta(recon_ctx *c, const recon_tile *tiles, int n, const int *variant,
-                      const int *order, size_t *bytes, unsigned *nblocks)
+                      const int *order, size_t *bytes, unsigned *nblocks, int *nfill)
 {
     const MetaLayout L = meta_layout(n);
     const size_t off_order = L.off_order, off_base = L.off_base, total = L.total;
@@ -308,12 +312,17 @@ static int stage_meta(recon_ctx *c, const recon_tile *tiles, int n, const int *v
     rk::TileDesc *D = (rk::TileDesc *)c->h_meta;
     int *ord = (int *)(c->h_meta + off_order);
     unsigned *base = (unsigned *)(c->h_meta + off_base);
+    int *fill = (int *)(c->h_meta + L.off_fill);
+    int nf = 0;
     unsigned long long nb = 0;
     for (int t = 0; t < n; ++t) {
         const recon_tile &T = tiles[t];
         rk::TileDesc d;
         memset(&d, 0, sizeof(d));
         d.I = T.I; d.J = T.J; d.H = T.H; d.W = T.W; d.pitch = T.pitch; d.conn = T.conn;
+        d.dual = T.op != RECON_OP_DILATE ? 1 : 0;
+        d.fill = T.op == RECON_OP_FILL_HOLES ? 1 : 0;
+        if (d.fill) fill[nf++] = t;
         d.nbx = (T.W + rk::BW - 1) / rk::BW;
         d.nby = (T.H + c->bh - 1) / c->bh;
         // variant: -1 = scans to stability; else k + 256 * (gain / 64)
@@ -355,8 +364,10 @@ static int stage_meta(recon_ctx *c, const recon_tile *tiles, int n, const int *v
         acc += (unsigned)(D[ord[i]].nbx * D[ord[i]].nby);
     }
     base[n] = acc;
+    memset(fill + nf, 0, sizeof(int) * (size_t)(n - nf));
     *bytes = total;
     *nblocks = (unsigned)nb;
+    *nfill = nf;
     return RECON_OK;
 }
 
@@ -379,8 +390,10 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
 
     size_t bytes = 0;
     unsigned nblocks = 0;
-    int rc = stage_meta(c, tiles, n, variant, order, &bytes, &nblocks);
+    int nfill = 0;
+    int rc = stage_meta(c, tiles, n, variant, order, &bytes, &nblocks, &nfill);
     if (rc) return rc;
+    if (nfill > 65535) return RECON_EINVAL;
 
     int grid = c->grid;
     if (!grid) {
@@ -477,6 +490,9 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
         cudaGraph_t g = nullptr;
         if (use_graph) CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaMemcpyAsync(c->d_meta, c->h_meta, bytes, cudaMemcpyHostToDevice, c->stream);
+        // FillHoles tiles: write their border markers first
+        if (e == cudaSuccess && nfill)
+            e = rk_launch_fill(P.tiles, (const int *)(c->d_meta + ML.off_fill), nfill, c->stream);
         if (e == cudaSuccess) e = rk_launch_init(std::min(grid, 4 * c->sms), &P, c->stream);
         // inside a capture, only an external record becomes a timed event node
         const unsigned evf = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -513,8 +529,13 @@ extern "C" int recon_batch(recon_ctx *c, const recon_tile *tiles, int n)
 
 extern "C" int recon_run(recon_ctx *c, const uint8_t *I, uint8_t *J, int H, int W, int conn)
 {
+    return recon_run_op(c, I, J, H, W, conn, RECON_OP_DILATE);
+}
+
+extern "C" int recon_run_op(recon_ctx *c, const uint8_t *I, uint8_t *J, int H, int W, int conn, int op)
+{
     recon_tile t;
-    t.I = I; t.J = J; t.H = H; t.W = W; t.pitch = W; t.conn = conn;
+    t.I = I; t.J = J; t.H = H; t.W = W; t.pitch = W; t.conn = conn; t.op = op;
     return batch_impl(c, &t, 1, nullptr, nullptr);
 }
 
@@ -595,7 +616,8 @@ extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
         const recon_tile &T = tiles[t];
         uint8_t *dI = c->d_img + off[t], *dJ = c->d_img + total + off[t];
         CK(cudaMemcpy2DAsync(dI, T.W, T.I, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpy2DAsync(dJ, T.W, T.J, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
+        if (T.op != RECON_OP_FILL_HOLES)   // a FillHoles tile's J is output only
+            CK(cudaMemcpy2DAsync(dJ, T.W, T.J, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
         dt[t] = T;
         dt[t].I = dI; dt[t].J = dJ; dt[t].pitch = T.W;
     }
@@ -614,7 +636,7 @@ extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
 extern "C" int recon_run_host(recon_ctx *c, const uint8_t *I, uint8_t *J, int H, int W, int conn)
 {
     recon_tile t;
-    t.I = I; t.J = J; t.H = H; t.W = W; t.pitch = W; t.conn = conn;
+    t.I = I; t.J = J; t.H = H; t.W = W; t.pitch = W; t.conn = conn; t.op = RECON_OP_DILATE;
     return recon_batch_host(c, &t, 1);
 }
 
@@ -629,7 +651,8 @@ extern "C" int recon_features(recon_ctx *c, const recon_tile *tiles, int n, floa
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
     std::vector<rl_tile> rt(n);
-    for (int t = 0; t < n; ++t) rt[t] = rl_tile{tiles[t].I, tiles[t].J, tiles[t].H, tiles[t].W, tiles[t].pitch};
+    for (int t = 0; t < n; ++t)
+        rt[t] = rl_tile{tiles[t].I, tiles[t].J, tiles[t].H, tiles[t].W, tiles[t].pitch, tiles[t].op};
     const size_t sb = rl_features_scratch(n), hb = rl_features_stage(n);
     void *d = nullptr, *h = nullptr;
     CK(cudaMalloc(&d, sb));

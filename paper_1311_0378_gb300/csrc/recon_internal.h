@@ -32,7 +32,8 @@ struct alignas(16) TileDesc {
                           // 2: also 16-byte rows: TMA loads through tmaps[2t], tmaps[2t+1]
     unsigned block_base;  // first global block index of this tile
     int gain;             // adaptive scan-to-queue switch: keep scanning while a pair raises >= gain px
-    int pad[2];
+    int dual;             // 1: erosion -- pixels are complemented (255 - v) as they are loaded and stored
+    int fill;             // 1: FillHoles -- J is first set to I on the image border, 255 inside
 };
 
 struct Ctl {

@@ -180,8 +180,36 @@ __device__ __forceinline__ unsigned smem_addr(const void *p)
 // shared memory; out-of-image pixels arrive as 0 (the border rule: absent
 // neighbours act as J = 0, the identity of max). One thread issues; every
 // thread waits on the CTA's mbarrier (bounded).
+// Bytes of the shared-memory word holding pixels x .. x+3 that lie inside
+// 0 <= x < W (the pixels of an erosion tile that get complemented).
+__device__ __forceinline__ uint32_t inimage_mask(int x, int W)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        if (x + b >= 0 && x + b < W) m |= 0xFFu << (8 * b);
+    return m;
+}
+
+// Erosion tiles (the dual operation) run as dilation on complemented values:
+// every loaded in-image pixel v becomes 255 - v (= ~v for a byte). Pixels
+// outside the image stay 0, i.e. absent, as for dilation.
 template <int BH>
-__device__ void tma_load_block(Smem<BH> &S, const Params &P, int t, int y0, int x0)
+__device__ void complement_box(Smem<BH> &S, const TileDesc &D, int y0, int x0)
+{
+    constexpr int NW = WR - WL + 1;
+    for (int idx = threadIdx.x; idx < (BH + 2) * NW; idx += NT) {
+        const int r = idx / NW, w = WL + (idx - r * NW);
+        const int yy = y0 - 1 + r;
+        if (yy < 0 || yy >= D.H) continue;
+        const uint32_t m = inimage_mask(x0 + 4 * (w - W0), D.W);
+        S.J[r * PW + w] ^= m;
+        S.I[r * PW + w] ^= m;
+    }
+}
+
+template <int BH>
+__device__ void tma_load_block(Smem<BH> &S, const Params &P, const TileDesc &D, int t, int y0, int x0)
 {
     const unsigned bar = smem_addr(&S.mbar);
     if (threadIdx.x == 0) {
@@ -207,6 +235,10 @@ __device__ void tma_load_block(Smem<BH> &S, const Params &P, int t, int y0, int 
     }
     __syncthreads();
     if (threadIdx.x == 0) S.phase = ph ^ 1u;
+    if (D.dual) {
+        complement_box(S, D, y0, x0);
+        __syncthreads();
+    }
     // halo mask out of the box, then zero it in S.I
     const uint8_t *Ib = (const uint8_t *)S.I;
     constexpr int RB = PW * 4;
@@ -241,22 +273,25 @@ __device__ void load_block(Smem<BH> &S, const TileDesc &D, int y0, int x0, bool 
         const bool hrow = (r == 0 || r == BH + 1), hword = (w == WL || w == WR);
         if (halo_only && !hrow && !hword) continue;
         const int yy = y0 - 1 + r;
-        uint32_t jv = 0, iv = 0;
+        uint32_t jv = 0, iv = 0, loaded = 0;   // loaded: the bytes read from the image
         const bool rowin = (yy >= 0 && yy < H);
         if (w == WL) {
             const int x = x0 - 1;
             if (rowin && x >= 0) {
                 jv = ld_j_byte(D.J + yy * pitch + x) << 24;
                 if (!halo_only) iv = ld_i_byte(D.I + yy * pitch + x) << 24;
+                loaded = 0xFF000000u;
             }
         } else if (w == WR) {
             const int x = x0 + BW;
             if (rowin && x < W) {
                 jv = ld_j_byte(D.J + yy * pitch + x);
                 if (!halo_only) iv = ld_i_byte(D.I + yy * pitch + x);
+                loaded = 0xFFu;
             }
         } else if (rowin) {
             const int x = x0 + 4 * (w - W0);
+            loaded = inimage_mask(x, W);
             if (D.fast && x + 3 < W) {
                 jv = ld_j_word(D.J + yy * pitch + x);
                 if (!halo_only) iv = ld_i_word(D.I + yy * pitch + x);
@@ -268,6 +303,7 @@ __device__ void load_block(Smem<BH> &S, const TileDesc &D, int y0, int x0, bool 
                     }
             }
         }
+        if (D.dual) { jv ^= loaded; iv ^= loaded; }   // erosion: complemented values
         S.J[r * PW + w] = jv;
         if (halo_only) continue;
         S.I[r * PW + w] = (hrow || hword) ? 0u : iv;
@@ -849,7 +885,7 @@ __device__ void write_back(Smem<BH> &S, const TileDesc &D, int y0, int x0)
         const int yy = y0 + r;
         if (yy >= D.H) break;
         const int x = x0 + 4 * lane;
-        const uint32_t v = S.J[(r + 1) * PW + lane + W0];
+        const uint32_t v = S.J[(r + 1) * PW + lane + W0] ^ (D.dual ? 0xFFFFFFFFu : 0u);
         uint8_t *dst = D.J + yy * pitch + x;
         if (D.fast && x + 3 < D.W) {
             *(uint32_t *)dst = v;
@@ -930,7 +966,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
 
     for (int i = threadIdx.x; i < BH / 32; i += NT) S.rowmask[i] = 0;
     if (threadIdx.x == 0) { S.notify = 0; S.flag = 0; }
-    if (D.fast == 2) tma_load_block(S, P, t, y0, x0);
+    if (D.fast == 2) tma_load_block(S, P, D, t, y0, x0);
     else load_block(S, D, y0, x0, false);
     __syncthreads();
     trace(P, 2, b);
@@ -1186,6 +1222,40 @@ __global__ void recon_init_kernel(Params P)
     }
 }
 
+// FillHoles tiles: J <- I on the one-pixel image border, 255 inside -- the
+// marker whose reconstruction by erosion under I fills the holes of I (the
+// flood of the background starts at the border). CTA (x, k) writes rows
+// x, x + gridDim.x, ... of tile list[k]; 16-byte stores where rows allow.
+__global__ void __launch_bounds__(256) fill_marker_kernel(const TileDesc *tiles, const int *list)
+{
+    const TileDesc D = tiles[list[blockIdx.y]];
+    const bool vec = (D.pitch % 16) == 0 && ((uintptr_t)D.I % 16) == 0 && ((uintptr_t)D.J % 16) == 0;
+    const int nv = vec ? D.W >> 4 : 0;
+    for (int y = blockIdx.x; y < D.H; y += gridDim.x) {
+        const uint8_t *irow = D.I + (size_t)y * D.pitch;
+        uint8_t *jrow = D.J + (size_t)y * D.pitch;
+        const bool edge_row = (y == 0 || y == D.H - 1);
+        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+            uint4 o;
+            if (edge_row) {
+                o = __ldg((const uint4 *)irow + v);
+            } else {
+                o = make_uint4(~0u, ~0u, ~0u, ~0u);
+                uint32_t *ow = (uint32_t *)&o;
+                const int x = 16 * v;
+                if (x == 0) ow[0] = (ow[0] & ~0xFFu) | irow[0];
+                if (x + 15 >= D.W - 1) {
+                    const int b = D.W - 1 - x;
+                    ow[b >> 2] = (ow[b >> 2] & ~(0xFFu << (8 * (b & 3)))) | ((uint32_t)irow[D.W - 1] << (8 * (b & 3)));
+                }
+            }
+            ((uint4 *)jrow)[v] = o;
+        }
+        for (int x = 16 * nv + threadIdx.x; x < D.W; x += blockDim.x)
+            jrow[x] = (edge_row || x == 0 || x == D.W - 1) ? irow[x] : (uint8_t)255;
+    }
+}
+
 }  // namespace rk
 
 // ---------------------------------------------------------------------------
@@ -1219,6 +1289,14 @@ extern "C" cudaError_t rk_configure(int bh, int *ctas_per_sm)
 extern "C" cudaError_t rk_launch_init(int grid, const rk::Params *P, cudaStream_t st)
 {
     rk::recon_init_kernel<<<grid, 256, 0, st>>>(*P);
+    return cudaGetLastError();
+}
+
+extern "C" cudaError_t rk_launch_fill(const rk::TileDesc *tiles, const int *list, int nlist, cudaStream_t st)
+{
+    if (nlist <= 0) return cudaSuccess;
+    if (nlist > 65535) return cudaErrorInvalidValue;
+    rk::fill_marker_kernel<<<dim3(64, (unsigned)nlist), 256, 0, st>>>(tiles, list);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,10 @@
 //
 //   features_kernel  one pass over I and J of every tile: 16-bin histogram of
 //                    I - J (bins of width 16), count of I >= 100 (blob pixels),
-//                    count of J == 0 (fill-holes markers), J > I violations
+//                    count of J == 0 (fill-holes markers), J > I violations.
+//                    Erosion tiles are counted on complemented values (the
+//                    dilation problem the kernel actually solves); FillHoles
+//                    tiles as complemented I with J = 0 (their interior marker)
 //   finalize_kernel  counts -> 20 fp32 features per tile
 //   mlp_forward      20 -> 64 -> 64 -> 2, ReLU hidden units, fp32
 //   mlp_grad         forward + backward of L = 1/(2N) sum (Y - T)^2 over a
@@ -18,7 +21,7 @@ namespace rl {
 
 struct FeatTile {
     const uint8_t *I, *J;
-    int H, W, pitch, pad;
+    int H, W, pitch, op;
 };
 
 __device__ __forceinline__ int find_chunk_tile(const unsigned *chunk_base, int n, unsigned c)
@@ -36,9 +39,14 @@ constexpr int NCOUNT = 19;
 constexpr int CHUNK_ROWS = 16;
 
 // Adds one pixel to the per-thread counts. The bin is matched against every
-// constant index so the counts stay in registers.
-__device__ __forceinline__ void count(unsigned (&loc)[NCOUNT], uint32_t i, uint32_t j)
+// constant index so the counts stay in registers. op: the tile's operation
+// (0 dilation, 1 erosion, 2 FillHoles), see the header comment.
+__device__ __forceinline__ void count(unsigned (&loc)[NCOUNT], uint32_t i, uint32_t j, int op)
 {
+    if (op != 0) {
+        i ^= 0xFFu;
+        j = (op == 2) ? 0u : (j ^ 0xFFu);
+    }
     const uint32_t bin = (j > i) ? 18u : ((i - j) >> 4);
 #pragma unroll
     for (int k = 0; k < 16; ++k) loc[k] += (bin == (uint32_t)k);
@@ -74,15 +82,15 @@ __global__ void __launch_bounds__(256) features_kernel(const FeatTile *T, int n,
 #pragma unroll
                         for (int s = 0; s < 4; ++s) {
                             const uint32_t i = (aw[q] >> (8 * s)) & 0xFF, j = (bw[q] >> (8 * s)) & 0xFF;
-                            count(loc, i, j);
+                            count(loc, i, j, d.op);
                         }
                 }
                 for (int x = (nv << 4) + threadIdx.x; x < d.W; x += blockDim.x) {
-                    count(loc, ri[x], rj[x]);
+                    count(loc, ri[x], rj[x], d.op);
                 }
             } else {
                 for (int x = threadIdx.x; x < d.W; x += blockDim.x) {
-                    count(loc, ri[x], rj[x]);
+                    count(loc, ri[x], rj[x], d.op);
                 }
             }
         }
@@ -237,7 +245,7 @@ cudaError_t rl_features(const rl_tile *tiles, int n, void *scratch, size_t scrat
     unsigned acc = 0;
     for (int t = 0; t < n; ++t) {
         F[t].I = tiles[t].I; F[t].J = tiles[t].J; F[t].H = tiles[t].H; F[t].W = tiles[t].W;
-        F[t].pitch = tiles[t].pitch; F[t].pad = 0;
+        F[t].pitch = tiles[t].pitch; F[t].op = tiles[t].op;
         base[t] = acc;
         acc += (unsigned)((tiles[t].H + rl::CHUNK_ROWS - 1) / rl::CHUNK_ROWS);
     }

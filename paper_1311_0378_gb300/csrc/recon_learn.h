@@ -10,6 +10,7 @@
 struct rl_tile {
     const uint8_t *I, *J;
     int H, W, pitch;
+    int op;   // RECON_OP_*: erosion and FillHoles tiles are described by their complemented values
 };
 
 size_t rl_features_scratch(int n);
