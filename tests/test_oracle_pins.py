@@ -277,7 +277,7 @@ def test_planted_mistake_fails_pins(name, tmp_path):
             % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                os.path.dirname(os.path.abspath(__file__)), str(so)))
     try:
-        rc = subprocess.run([sys.executable, "-c", code], timeout=60).returncode
+        rc = subprocess.run([sys.executable, "-c", code], timeout=15).returncode
     except subprocess.TimeoutExpired:
         rc = "timeout"
     assert rc != 0, "planted mistake not caught: " + name

@@ -252,7 +252,7 @@ def test_planted_erosion_mistake_fails_pins(name, tmp_path):
             "import test_oracle_pins_dual as T; sys.exit(T._mutant_runner(%r))"
             % (os.path.dirname(here), here, str(so)))
     try:
-        rc = subprocess.run([sys.executable, "-c", code], timeout=60).returncode
+        rc = subprocess.run([sys.executable, "-c", code], timeout=15).returncode
     except subprocess.TimeoutExpired:
         rc = "timeout"
     assert rc != 0, "planted mistake not caught: " + name
