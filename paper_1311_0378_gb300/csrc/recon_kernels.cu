@@ -710,19 +710,17 @@ __device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t 
     constexpr int RB = PW * 4;
     const int off8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
     const int off4[4] = {-RB, -1, 1, RB};
-    uint32_t cv[CONN];
+    // The neighbour's whole word is read once: its byte decides the
+    // propagation condition and the word is the expected value of the
+    // compare-and-swap (one dependent shared-memory round trip fewer).
+    uint32_t cv[CONN], old[CONN], seen[CONN];
     unsigned cand = 0;
 #pragma unroll
     for (int k = 0; k < CONN; ++k) {
         const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
         cv[k] = min(v, (uint32_t)Ib[q]);
-        if (act && Jb[q] < cv[k]) cand |= 1u << k;
-    }
-    uint32_t old[CONN], seen[CONN];
-#pragma unroll
-    for (int k = 0; k < CONN; ++k) {
-        const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
-        old[k] = ((cand >> k) & 1u) ? ((const volatile uint32_t *)Jw)[q >> 2] : 0u;
+        old[k] = ((const volatile uint32_t *)Jw)[q >> 2];
+        if (act && ((old[k] >> ((q & 3) * 8)) & 0xFFu) < cv[k]) cand |= 1u << k;
     }
 #pragma unroll
     for (int k = 0; k < CONN; ++k) {
@@ -730,10 +728,7 @@ __device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t 
         if ((cand >> k) & 1u) {
             const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
             const unsigned sh = (q & 3) * 8;
-            if (((old[k] >> sh) & 0xFFu) < cv[k])
-                seen[k] = atomicCAS(Jw + (q >> 2), old[k], (old[k] & ~(0xFFu << sh)) | (cv[k] << sh));
-            else
-                cand &= ~(1u << k);   // someone raised it meanwhile
+            seen[k] = atomicCAS(Jw + (q >> 2), old[k], (old[k] & ~(0xFFu << sh)) | (cv[k] << sh));
         }
     }
     unsigned raised = 0;
