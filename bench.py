@@ -297,6 +297,54 @@ def compare_schedules(rc, ctx, stream, Is, Js, J0, tiles, desc, px, flush, args)
     return res
 
 
+def run_microbench(args):
+    """--microbench: the GB300 versions of Tables III and IV (random 32-bit
+    reads / writes in a matrix; atomic adds on one variable or an array), in
+    the paper's configuration (4K x 4K matrix, 10 million operations) and in
+    an HBM-sized one (2^30 elements, 4 GiB). One JSON line."""
+    import torch
+    import paper_1311_0378_gb300 as rc
+    from paper_1311_0378_gb300 import build as rbuild
+    rbuild.build()
+    torch.cuda.set_device(0)
+    reps = max(args.steps, 3)
+    res = {}
+    for name, log2n, ops in (("paper_4Kx4K", 24, 10_000_000), ("hbm_4GiB", 30, 100_000_000)):
+        M = torch.zeros(1 << log2n, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        for write in (False, True):
+            times = []
+            for r in range(reps + 1):
+                st, _, ms = rc.recon_mb_random(M.data_ptr(), log2n, ops, write, 1000 + r)
+                rc.check(st, "recon_mb_random")
+                if r:
+                    times.append(ms)
+            ms = statistics.median(times)
+            res["%s_random_%s_MBps" % (name, "write" if write else "read")] = round(ops * 4 / (ms / 1e3) / 1e6, 1)
+            res["%s_random_%s_Mops" % (name, "write" if write else "read")] = round(ops / (ms / 1e3) / 1e6, 1)
+        del M
+    threads = rc.recon_mb_threads(0)
+    C = torch.zeros(threads, dtype=torch.int32, device="cuda")
+    for mode, label, iters in ((0, "global_single_variable", 64), (1, "global_array", 256),
+                               (2, "shared_single_word_per_cta", 256), (3, "shared_array", 1024)):
+        times = []
+        for r in range(reps + 1):
+            C.zero_()
+            torch.cuda.synchronize()
+            st, ms = rc.recon_mb_atomic(C.data_ptr(), mode, iters)
+            rc.check(st, "recon_mb_atomic")
+            if r:
+                times.append(ms)
+        res["atomic_add_%s_Mops" % label] = round(threads * iters / (statistics.median(times) / 1e3) / 1e6, 1)
+    line = {"metric": "device micro-benchmarks (Tables III-IV)", "unit": "MB/s and Mops/s", "n_gpus": 1,
+            "steps": reps, "data": "synthetic", "config": {"threads": threads, "timing": "CUDA events, median"},
+            "results": res,
+            "paper_gpu": {"random_read_MBps": 895, "random_write_MBps": 126,
+                          "atomic_single_variable_Mops": 693, "atomic_array_Mops": 38630}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,9 +367,13 @@ def main():
     ap.add_argument("--schedule", default="learned", choices=["learned", "plain"],
                     help="learned: the cost model picks each tile's variant and the packing order "
                          "(planning runs inside every timed step); plain: context defaults")
+    ap.add_argument("--microbench", action="store_true",
+                    help="run the random-access and atomic micro-benchmarks (Tables III-IV) instead")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.microbench:
+        return run_microbench(args)
 
     import torch
     import paper_1311_0378_gb300 as rc

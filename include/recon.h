@@ -265,6 +265,38 @@ int recon_sched_set_model(recon_ctx *ctx, const float *theta, const float *norm,
 int recon_sched_plan_batch(recon_ctx *ctx, const recon_tile *tiles, int n, int *variant, int *order,
                            float *pred);
 
+/* ---- device micro-benchmarks (Sec. V-B, Tables III and IV) ----
+ * GB300 versions of the paper's random-access and atomic micro-benchmarks,
+ * which bound the irregular (wavefront) phase. Both run on the CURRENT CUDA
+ * device and its default stream, wait for completion, and return the kernel's
+ * CUDA-event time in *ms. They allocate at most 8 bytes of scratch. */
+
+/* Number of threads the micro-benchmark kernels launch on `device`
+ * (SMs x 8 CTAs x 256), or a negative status. */
+int recon_mb_threads(int device);
+
+/* Table III: `ops` random 32-bit accesses to the device matrix `matrix` of
+ * 2^log2n elements (1 <= log2n <= 34; the paper's 4K x 4K matrix is log2n = 24).
+ * Access k (k = 0 .. ops-1) goes to element SplitMix64(seed, k + 1) >> (64 - log2n),
+ * where SplitMix64(s, n) is output n of the SplitMix64 generator seeded with s
+ * (s + n * 0x9E3779B97F4A7C15, then the generator's published mixing steps).
+ * write = 0: reads; *checksum receives the sum of the values read (mod 2^64).
+ * write = 1: element i is set to (uint32)(i * 0x9E3779B1) ^ 0x5A5A5A5A (a value of
+ * the index only, so colliding writes agree); checksum may be NULL.
+ * Bandwidth = ops * 4 bytes / *ms. */
+int recon_mb_random(const void *matrix, int log2n, uint64_t ops, int write, uint64_t seed,
+                    uint64_t *checksum, float *ms);
+
+/* Table IV: every thread performs `iters` atomic adds of 1.
+ *   mode 0: all threads on counters[0] (one variable, global memory);
+ *   mode 1: thread t on counters[t] (an array indexed by thread, global);
+ *   mode 2: all threads of a CTA on one shared-memory word; the CTA then writes
+ *           its total to counters[cta];
+ *   mode 3: each thread on its own shared-memory word, written to counters[t].
+ * counters: device array of recon_mb_threads(device) entries, zeroed by the
+ * caller for modes 0 and 1. Throughput = threads * iters / *ms. */
+int recon_mb_atomic(unsigned *counters, int mode, int iters, float *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@ SYMBOLS = ("recon_init", "recon_run", "recon_run_op", "recon_batch", "recon_batc
            "recon_strerror", "recon_set_param", "recon_get_param", "recon_get_work",
            "recon_last_kernel_ms", "recon_features", "recon_mlp_forward", "recon_mlp_grad",
            "recon_mlp_adam", "recon_mlp_train", "recon_sched_set_model", "recon_sched_plan_batch",
-           "recon_autotune", "recon_sync_for", "recon_trace", "recon_run_noalloc")
+           "recon_autotune", "recon_sync_for", "recon_trace", "recon_run_noalloc",
+           "recon_mb_threads", "recon_mb_random", "recon_mb_atomic")
 RECON_NFEAT, RECON_MLP_NPARAMS = 20, 5634
 
 
@@ -94,6 +95,10 @@ def lib() -> ctypes.CDLL:
         "recon_sync_for": ([vp, i], i),
         "recon_trace": ([vp, vp, i], i),
         "recon_run_noalloc": ([vp, vp, i, i, i, vp], i),
+        "recon_mb_threads": ([i], i),
+        "recon_mb_random": ([vp, i, ctypes.c_uint64, i, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
+                             ctypes.POINTER(ctypes.c_float)], i),
+        "recon_mb_atomic": ([vp, i, i, ctypes.POINTER(ctypes.c_float)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -264,3 +269,24 @@ def recon_trace(ctx, n: int):
 def recon_run_noalloc(I: int, J: int, H: int, W: int, conn: int, stream: int = 0) -> int:
     """Allocation-free single-tile reconstruction (device pointers; waits)."""
     return lib().recon_run_noalloc(I, J, H, W, conn, ctypes.c_void_p(stream or None))
+
+
+# ---- device micro-benchmarks (current device, default stream; they wait) ----
+
+def recon_mb_threads(device: int = 0) -> int:
+    return lib().recon_mb_threads(device)
+
+
+def recon_mb_random(matrix: int, log2n: int, ops: int, write: bool, seed: int):
+    """Returns (status, checksum or None, ms)."""
+    cs = ctypes.c_uint64(0)
+    ms = ctypes.c_float(0)
+    rc = lib().recon_mb_random(matrix, log2n, ops, 1 if write else 0, seed, ctypes.byref(cs), ctypes.byref(ms))
+    return rc, (None if write else cs.value), ms.value
+
+
+def recon_mb_atomic(counters: int, mode: int, iters: int):
+    """Returns (status, ms)."""
+    ms = ctypes.c_float(0)
+    rc = lib().recon_mb_atomic(counters, mode, iters, ctypes.byref(ms))
+    return rc, ms.value
