@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "recon_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "dt_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, EINVAL, EMARKER, ENOMEM = 0, 1, 2, 3
@@ -30,10 +31,10 @@ OK, EINVAL, EMARKER, ENOMEM = 0, 1, 2, 3
 
 def build(force: bool = False) -> str:
     """Compiles liboracle.so (plain C, -O2, no vector intrinsics)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               "-o", tmp, _SRC])
+                               "-o", tmp, *_SRCS])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -57,6 +58,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_recon_erode.argtypes = [u8p, u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]
         L.oracle_erode_step.argtypes = [u8p, u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.oracle_dt.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_dt.restype = ctypes.c_int
         for f in (L.oracle_recon, L.oracle_recon_widest, L.oracle_dilate_step, L.oracle_recon_tiles,
                   L.oracle_recon_erode, L.oracle_erode_step):
             f.restype = ctypes.c_int
@@ -140,6 +143,24 @@ def fill_holes(I: np.ndarray, conn: int = 8) -> np.ndarray:
     M = np.zeros_like(C)
     M[0, :], M[-1, :], M[:, 0], M[:, -1] = C[0, :], C[-1, :], C[:, 0], C[:, -1]
     return (255 - recon(C, M, conn).astype(np.int16)).astype(np.uint8)
+
+
+def distance_transform(B: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """Distance transform by irregular wavefront propagation (Table II; Algorithm
+    1 with nearest-background-site elements, 8-connected, FIFO order; see
+    dt_oracle.c). B: 2-D array, nonzero = foreground. Returns (site, d2):
+    int32 index y*W+x of the site found for each pixel (-1 if the image has no
+    background) and uint32 squared Euclidean distance to it (0 on background,
+    0xFFFFFFFF without a site)."""
+    B = np.ascontiguousarray(B != 0, dtype=np.uint8)
+    if B.ndim != 2:
+        raise ValueError("B must be a 2-D array")
+    site = np.empty(B.shape, np.int32)
+    d2 = np.empty(B.shape, np.uint32)
+    rc = lib().oracle_dt(B.ctypes.data, B.shape[0], B.shape[1], site.ctypes.data, d2.ctypes.data)
+    if rc != OK:
+        raise ValueError("oracle_dt status %d" % rc)
+    return site, d2
 
 
 def recon_tiles(pairs: Sequence[Tuple[np.ndarray, np.ndarray]], conns: Sequence[int],
