@@ -265,6 +265,27 @@ int recon_sched_set_model(recon_ctx *ctx, const float *theta, const float *norm,
 int recon_sched_plan_batch(recon_ctx *ctx, const recon_tile *tiles, int n, int *variant, int *order,
                            float *pred);
 
+/* ---- distance transform (Table II) ----
+ * For each foreground pixel (B != 0) of the H x W image B (device uint8,
+ * pitch = W), the squared Euclidean distance to the background pixel that the
+ * 8-connected irregular wavefront propagation assigns to it: Algorithm 1 with
+ * elements D(p) = the nearest background pixel ("site") found so far, seeded
+ * from the background pixels that touch the foreground; a foreground neighbour
+ * q takes site s when (|q - s|^2, s) < (|q - site(q)|^2, site(q)).
+ * d2: device uint32 H x W out (0 on background; 0xFFFFFFFF everywhere when B
+ * has no background pixel). site: device int32 H x W out, index y*W + x of the
+ * assigned background pixel (-1 without background), or NULL (the context then
+ * keeps it in its scratch). 1 <= H, W <= 32768, H * W < 2^31.
+ * Like Danielsson's vector propagation this approximates the exact Euclidean
+ * transform (a pixel passes on only the site it holds); the result depends on
+ * the processing order, but every site is a background pixel and no pixel has
+ * an 8-neighbour holding a closer site. Runs on the context stream and waits;
+ * RECON_ETIMEOUT if an iteration bound ran out. */
+int recon_dt(recon_ctx *ctx, const uint8_t *B, uint32_t *d2, int32_t *site, int H, int W);
+
+/* Wavefront levels the last recon_dt call ran (diagnostics), or -1. */
+int recon_dt_levels(recon_ctx *ctx);
+
 /* ---- device micro-benchmarks (Sec. V-B, Tables III and IV) ----
  * GB300 versions of the paper's random-access and atomic micro-benchmarks,
  * which bound the irregular (wavefront) phase. Both run on the CURRENT CUDA

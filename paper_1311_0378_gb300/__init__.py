@@ -31,7 +31,7 @@ SYMBOLS = ("recon_init", "recon_run", "recon_run_op", "recon_batch", "recon_batc
            "recon_last_kernel_ms", "recon_features", "recon_mlp_forward", "recon_mlp_grad",
            "recon_mlp_adam", "recon_mlp_train", "recon_sched_set_model", "recon_sched_plan_batch",
            "recon_autotune", "recon_sync_for", "recon_trace", "recon_run_noalloc",
-           "recon_mb_threads", "recon_mb_random", "recon_mb_atomic")
+           "recon_mb_threads", "recon_mb_random", "recon_mb_atomic", "recon_dt", "recon_dt_levels")
 RECON_NFEAT, RECON_MLP_NPARAMS = 20, 5634
 
 
@@ -96,6 +96,8 @@ def lib() -> ctypes.CDLL:
         "recon_trace": ([vp, vp, i], i),
         "recon_run_noalloc": ([vp, vp, i, i, i, vp], i),
         "recon_mb_threads": ([i], i),
+        "recon_dt": ([vp, vp, vp, vp, i, i], i),
+        "recon_dt_levels": ([vp], i),
         "recon_mb_random": ([vp, i, ctypes.c_uint64, i, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_float)], i),
         "recon_mb_atomic": ([vp, i, i, ctypes.POINTER(ctypes.c_float)], i),
@@ -290,3 +292,12 @@ def recon_mb_atomic(counters: int, mode: int, iters: int):
     ms = ctypes.c_float(0)
     rc = lib().recon_mb_atomic(counters, mode, iters, ctypes.byref(ms))
     return rc, ms.value
+
+
+def recon_dt(ctx, B: int, d2: int, site: int, H: int, W: int) -> int:
+    """Distance transform (device addresses; site may be 0); waits."""
+    return lib().recon_dt(ctx, B, d2, ctypes.c_void_p(site or None), H, W)
+
+
+def recon_dt_levels(ctx) -> int:
+    return lib().recon_dt_levels(ctx)

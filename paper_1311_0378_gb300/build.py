@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librecon.so")
 SOURCES = ["recon_kernels.cu", "recon_api.cu", "recon_sched.cu", "recon_learn.cu", "recon_noalloc.cu",
-           "recon_mb.cu"]
+           "recon_mb.cu", "recon_dt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

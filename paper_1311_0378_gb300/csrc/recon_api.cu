@@ -15,6 +15,7 @@
 #include "recon_internal.h"
 #include "recon_sched.h"
 #include "recon_learn.h"
+#include "recon_dt.h"
 
 extern "C" size_t rk_smem_bytes(int bh);
 extern "C" cudaError_t rk_configure(int bh, int *ctas_per_sm);
@@ -54,6 +55,11 @@ struct recon_ctx {
     std::vector<unsigned char> gsig;
     // learned scheduler
     recon_sched *sched = nullptr;
+    // distance transform scratch
+    unsigned char *d_dt = nullptr; size_t cap_dt = 0;
+    int *d_dt_site = nullptr; size_t cap_dt_site = 0;
+    unsigned *h_dt_cnt = nullptr;
+    int dt_levels = 0;
 };
 
 static int cuda_status(cudaError_t e)
@@ -138,6 +144,9 @@ extern "C" int recon_free(recon_ctx *c)
     cudaFree(c->d_work);
     cudaFree(c->d_spill);
     cudaFree(c->d_img);
+    cudaFree(c->d_dt);
+    cudaFree(c->d_dt_site);
+    if (c->h_dt_cnt) cudaFreeHost(c->h_dt_cnt);
     if (c->h_meta) cudaFreeHost(c->h_meta);
     if (c->h_trace) cudaFreeHost(c->h_trace);
     if (c->meta_free) cudaEventDestroy(c->meta_free);
@@ -871,4 +880,33 @@ extern "C" int recon_trace(recon_ctx *c, unsigned *out, int n)
     const int m = (int)std::min((size_t)n, c->cap_trace);
     for (int i = 0; i < m; ++i) out[i] = ((volatile unsigned *)c->h_trace)[i];
     return m;
+}
+
+// ---------------------------------------------------------------------------
+// distance transform (recon_dt.cu)
+
+extern "C" int recon_dt(recon_ctx *c, const uint8_t *B, uint32_t *d2, int32_t *site, int H, int W)
+{
+    if (!c || !B || !d2 || H < 1 || W < 1 || H > 32768 || W > 32768) return RECON_EINVAL;
+    if ((long long)H * W > 0x7FFFFFFFll) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    const size_t n = (size_t)H * W;
+    const size_t need = dt_scratch_bytes(H, W);
+    if (c->cap_dt < need || (!site && c->cap_dt_site < n) || !c->h_dt_cnt) {
+        CK(cudaStreamSynchronize(c->stream));
+        int rc;
+        if ((rc = grow(&c->d_dt, &c->cap_dt, need))) return rc;
+        if (!site && (rc = grow(&c->d_dt_site, &c->cap_dt_site, n))) return rc;
+        if (!c->h_dt_cnt) CK(cudaMallocHost((void **)&c->h_dt_cnt, 4 * sizeof(unsigned)));
+    }
+    int *s = site ? (int *)site : c->d_dt_site;
+    const int rc = dt_run(B, H, W, s, (unsigned *)d2, c->d_dt, c->h_dt_cnt, 8 * c->sms, c->stream, &c->dt_levels);
+    if (rc == DT_ECUDA) return RECON_ECUDA;
+    CK(cudaStreamSynchronize(c->stream));
+    return rc == DT_ELIMIT ? RECON_ETIMEOUT : RECON_OK;
+}
+
+extern "C" int recon_dt_levels(recon_ctx *c)
+{
+    return c ? c->dt_levels : -1;
 }
