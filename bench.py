@@ -36,8 +36,9 @@ sys.path.insert(0, ROOT)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # compulsory traffic per pixel: read I, read J, write R (reconstruction by
 # dilation or erosion); read I, write the result (FillHoles)
-ALG_BYTES_PER_PX = {"dilate": 3, "erode": 3, "fill_holes": 2}
+ALG_BYTES_PER_PX = {"dilate": 3, "erode": 3, "fill_holes": 2, "dt": 5}
 OP_CODE = {"dilate": 0, "erode": 1, "fill_holes": 2}
+OPS = sorted(list(OP_CODE) + ["dt"])
 
 
 def kernel_hash():
@@ -189,6 +190,7 @@ def cpu_baseline(w, tiles, shared_mask, budget_tiles=None, op="dilate"):
 
 def run_reference(args):
     """--impl reference: the CPU oracle timed as the reference arm."""
+    import numpy as np
     import oracle
     import synth
     rank = int(os.environ.get("RANK", "0"))
@@ -204,6 +206,11 @@ def run_reference(args):
         if args.op == "erode":
             I, J = 255 - I, 255 - J
         t0 = time.perf_counter()
+        if args.op == "dt":
+            B = np.ascontiguousarray((I >= 100) if i % 2 == 0 else (I < 100), dtype=np.uint8)
+            t0 = time.perf_counter()
+            oracle.distance_transform(B)
+            return time.perf_counter() - t0, t.H * t.W
         if args.op == "erode":
             oracle.recon_erode(I, J, t.conn)
         elif args.op == "fill_holes":
@@ -219,7 +226,8 @@ def run_reference(args):
         tot_t += dt
         tot_px += px
     v = tot_px / tot_t / 1e6
-    line = {"impl": "reference", "metric": "reconstructed Mpix/s", "value": round(v, 3),
+    metric = "distance-transformed Mpix/s" if args.op == "dt" else "reconstructed Mpix/s"
+    line = {"impl": "reference", "metric": metric, "value": round(v, 3),
             "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1000 * tot_t / max(args.steps, 1), 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
@@ -345,6 +353,106 @@ def run_microbench(args):
     return 0
 
 
+def dt_masks(w, tiles):
+    """Distance-transform inputs: the objects (blob pixels, I >= 100) of each
+    distinct mask of the workload, and the space between them (I < 100)."""
+    import numpy as np
+    import synth
+    masks, seen = [], set()
+    for t in tiles:
+        I, _ = synth.tile_pair(t, w.seed)
+        h = hash(I[::97, ::89].tobytes())
+        if h in seen:
+            continue
+        seen.add(h)
+        masks.append(np.ascontiguousarray(I >= 100, dtype=np.uint8))
+        masks.append(np.ascontiguousarray(I < 100, dtype=np.uint8))
+    return masks
+
+
+def run_dt(args):
+    """--op dt: the distance transform (Table II) on the workload's masks."""
+    import numpy as np
+    import torch
+    import paper_1311_0378_gb300 as rc
+    from paper_1311_0378_gb300 import build as rbuild
+    rbuild.build()
+    torch.cuda.set_device(0)
+    w, tiles, _ = workload_tiles(args.workload)
+    masks = dt_masks(w, tiles[:8])
+    px = sum(m.size for m in masks)
+    ctx = rc.recon_init(0, 0, 0)
+    dB = [torch.from_numpy(m).cuda() for m in masks]
+    d2 = [torch.empty(m.shape, dtype=torch.int32, device="cuda") for m in masks]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        for b, d in zip(dB, d2):
+            rc.check(rc.recon_dt(ctx, b.data_ptr(), d.data_ptr(), 0, b.shape[0], b.shape[1]), "recon_dt")
+    launches = 0
+    for b, d in zip(dB, d2):   # per mask: init, the level launches (batches of 16), final
+        rc.check(rc.recon_dt(ctx, b.data_ptr(), d.data_ptr(), 0, b.shape[0], b.shape[1]), "recon_dt")
+        launches += 2 + rc.recon_dt_levels(ctx)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    times = []
+    with Clocks(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    levels = rc.recon_dt_levels(ctx)
+    # end to end: host mask in, host distances out
+    hd2 = [torch.empty(m.shape, dtype=torch.int32).pin_memory() for m in masks]
+    hB = [torch.from_numpy(m).pin_memory() for m in masks]
+    e2e = []
+    for i in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b, hb, d, hd in zip(dB, hB, d2, hd2):
+            b.copy_(hb, non_blocking=True)
+            torch.cuda.synchronize()
+            rc.check(rc.recon_dt(ctx, b.data_ptr(), d.data_ptr(), 0, b.shape[0], b.shape[1]), "recon_dt")
+            hd.copy_(d)
+        e2e.append(time.perf_counter() - t0)
+    rc.recon_free(ctx)
+    ms = statistics.mean(times)
+    pk, src = peaks()
+    achieved = ALG_BYTES_PER_PX["dt"] * px / (ms / 1e3) / 1e9
+    line = {"metric": "distance-transformed Mpix/s", "value": round(px / (ms / 1e3) / 1e6, 2), "unit": "Mpix/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "op": "dt", "masks": len(masks), "pixels_per_step": px,
+                       "objects": "blob pixels (I >= 100) and the space between them (I < 100)",
+                       "l2": "flushed before each timed step (512 MiB write)", "levels_last_mask": levels},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(achieved / pk["hbm_gbs"], 5), "traffic": None,
+                         "alg_bytes_per_px": ALG_BYTES_PER_PX["dt"], "peak_source": src,
+                         "note": "step time includes the host reads of the level counters"},
+            "e2e": {"value": round(px / statistics.median(e2e) / 1e6, 2), "unit": "Mpix/s",
+                    "h2d_bytes_per_step": px, "d2h_bytes_per_step": 4 * px},
+            "gpu_launches": launches * args.steps, "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=len(masks)) as ex:
+            list(ex.map(oracle.distance_transform, masks))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": round(px / dt / 1e6, 3), "unit": "Mpix/s", "cores": len(masks),
+                                "kind": "oracle", "sample": "all %d masks, full size" % len(masks),
+                                "seconds": round(dt, 2)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,7 +461,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="single4096",
                     choices=["single4096", "single512", "batch64", "uneven1000"])
-    ap.add_argument("--op", default="dilate", choices=sorted(OP_CODE),
+    ap.add_argument("--op", default="dilate", choices=OPS,
                     help="dilate: reconstruction by dilation; erode: by erosion (complemented pairs); "
                          "fill_holes: FillHoles of the masks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -374,6 +482,8 @@ def main():
         return run_reference(args)
     if args.microbench:
         return run_microbench(args)
+    if args.op == "dt":
+        return run_dt(args)
 
     import torch
     import paper_1311_0378_gb300 as rc
