@@ -6,8 +6,8 @@
  * image J limited by a mask image I, 4- or 8-connected, after Vincent 1993):
  *     R = lim_n delta_I^n(J),   delta_I(X)(p) = min( max_{q in N(p)} X(q), I(p) ),
  * N(p) = p and its 4 or 8 neighbours inside the image. R is computed by the
- * irregular wavefront propagation pattern (Sec. III-B, Algorithm 1) in the
- * hybrid form of Sec. VI-B (irregular operations): raster / anti-raster scans
+ * irregular wavefront propagation pattern (Sec. II-B, Algorithm 1) in the
+ * hybrid form of Sec. V-C (irregular operations): raster / anti-raster scans
  * first, then queue-driven propagation. R is unique, so every schedule returns
  * the same bytes.
  *
@@ -88,7 +88,7 @@ typedef struct {
 int recon_init(recon_ctx **ctx, int device, void *cuda_stream, unsigned flags);
 
 /* Reconstructs one tile (Table II; Algorithm 1 with the hybrid scan + queue
- * schedule of Sec. VI-B). I, J: device pointers, pitch = W. J <- R in place. */
+ * schedule of Sec. V-C). I, J: device pointers, pitch = W. J <- R in place. */
 int recon_run(recon_ctx *ctx, const uint8_t *I, uint8_t *J, int H, int W, int conn);
 
 /* recon_run for any operation: op = RECON_OP_DILATE, RECON_OP_ERODE (J >= I,
@@ -212,7 +212,7 @@ int recon_run_noalloc(const uint8_t *I, uint8_t *J, int H, int W, int conn, void
  * device backup before every run), installs the fastest in the context and
  * writes it to best[4] = {block height, bands, scan pairs, scan gain}. J
  * holds its original marker on return. The paper tunes its scan-to-queue
- * switch point the same way (Sec. VI-B). */
+ * switch point the same way (Sec. V-C). */
 int recon_autotune(recon_ctx *ctx, const recon_tile *tiles, int n, int reps, int *best);
 
 /* ---- learned cost model ------------------------------------------------
@@ -286,7 +286,7 @@ int recon_dt(recon_ctx *ctx, const uint8_t *B, uint32_t *d2, int32_t *site, int 
 /* Wavefront levels the last recon_dt call ran (diagnostics), or -1. */
 int recon_dt_levels(recon_ctx *ctx);
 
-/* ---- device micro-benchmarks (Sec. V-B, Tables III and IV) ----
+/* ---- device micro-benchmarks (Sec. V-C, Tables III and IV) ----
  * GB300 versions of the paper's random-access and atomic micro-benchmarks,
  * which bound the irregular (wavefront) phase. Both run on the CURRENT CUDA
  * device and its default stream, wait for completion, and return the kernel's

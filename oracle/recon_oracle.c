@@ -10,7 +10,7 @@
  * N(p) = p plus its 4 or 8 neighbours that lie inside the image.
  * Precondition J <= I pixel-wise (otherwise status 2 and J is left untouched).
  *
- * oracle_recon        -- the method's regular phase (Sec. VI-B, irregular
+ * oracle_recon        -- the method's regular phase (Sec. V-C, irregular
  *                        operations: raster / anti-raster scans) run alone until
  *                        a full raster + anti-raster pair changes no pixel.
  * oracle_recon_widest -- an independent exact route used as a cross-check and for

@@ -1,6 +1,6 @@
 // Grayscale morphological reconstruction by irregular wavefront propagation
-// (Table II "Morphological Reconstruction"; Sec. III-B Algorithm 1; the hybrid
-// scan-then-queue schedule of Sec. VI-B) for sm_103a.
+// (Table II "Morphological Reconstruction"; Sec. II-B Algorithm 1; the hybrid
+// scan-then-queue schedule of Sec. V-C) for sm_103a.
 //
 // Design. The image is cut into blocks of BH x 128 pixels. One persistent
 // launch pulls blocks from a work list: first every block once, in packing
@@ -995,7 +995,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
     // A revisit seeds from its frame first; only when that raised many frame
     // pixels (a wide change arrived through the halo) does it switch to scan
     // pairs -- fixed ones, then more while a pair still raises at least gain
-    // pixels (the tuned scan-to-queue switch, Sec. VI-B) -- and seed the whole block.
+    // pixels (the tuned scan-to-queue switch, Sec. V-C) -- and seed the whole block.
     const bool scan_on_revisit = k >= 0 && (P.revisit_scans > 0 || D.gain > 0);
     auto revisit_scans = [&]() {
         for (int s = 0; s < MAX_ADAPTIVE; ++s) {

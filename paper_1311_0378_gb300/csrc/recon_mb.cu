@@ -1,5 +1,5 @@
 // GB300 versions of the paper's two device micro-benchmarks, which explain the
-// irregular operations' performance (Sec. V-B):
+// irregular operations' performance (Sec. V-C):
 //   Table III -- bandwidth of random 32-bit reads / writes in a 4K x 4K matrix
 //                of integers (10 million operations);
 //   Table IV  -- throughput of atomic adds, (1) every thread on one variable,
