@@ -128,6 +128,10 @@ __device__ void notify_block(const Params &P, unsigned a)
     }
 }
 
+#ifndef IDLE_SLEEP_MAX_NS
+#define IDLE_SLEEP_MAX_NS 4096   // longest back-off of an idle CTA between polls
+#endif
+
 // Thread 0: next block to process, or EMPTY when all work is done / aborted.
 __device__ unsigned next_item(const Params &P)
 {
@@ -159,7 +163,7 @@ __device__ unsigned next_item(const Params &P)
         if (idle0 == 0) idle0 = now;
         else if ((long long)(now - idle0) > P.wait_ns) { set_abort(P, AB_IDLE); return EMPTY; }
         __nanosleep(sleep);
-        if (sleep < 4096) sleep <<= 1;
+        if (sleep < IDLE_SLEEP_MAX_NS) sleep <<= 1;
     }
 }
 
