@@ -453,6 +453,49 @@ def run_dt(args):
     return 0
 
 
+def phase_rooflines(rc, ctx, stream, Js, J0, desc, tiles, px, flush):
+    """The scan (sweep) and queue halves of the method, each timed on its own
+    over the same batch, with its own roofline: the sweeps-only variant moves
+    3 bytes per pixel per directional pass (read I and J, write J; 128-pixel
+    block rows counted by the kernel) against the measured HBM copy bandwidth;
+    the queue-first variant (no scan pairs) checks |N| neighbours per wavefront
+    entry, each a shared-memory access or compare-and-swap, against the
+    shared-memory atomic-add rate measured here by the micro-benchmark."""
+    import torch
+    n = len(desc)
+    order = sorted(range(n), key=lambda i: -desc[i][2] * desc[i][3])
+    pk, src = peaks()
+    out = {}
+    for name, var in (("sweeps_only", -1), ("queue_first", 0)):
+        def run(v=var):
+            rc.check(rc.recon_batch_ex(ctx, desc, [v] * n, order), name)
+        ms = time_fn(run, stream, Js, J0, flush)
+        kms = rc.recon_last_kernel_ms(ctx)
+        w = rc.recon_get_work(ctx, n)
+        rows = sum(x["scan_rows"] for x in w)
+        pops = sum(x["pops"] for x in w)
+        res = {"mpix_s": round(px / ms / 1e3, 1), "kernel_ms": round(kms, 3), "scan_rows": rows, "pops": pops}
+        if name == "sweeps_only":
+            gbs = rows * 128 * 3 / (kms / 1e3) / 1e9
+            res.update({"bound": "hbm", "achieved_GBps": round(gbs, 1), "peak_GBps": pk["hbm_gbs"],
+                        "frac": round(gbs / pk["hbm_gbs"], 4), "bytes_per_row_px": 3})
+        else:
+            checks = sum(x["pops"] * t.conn for x, t in zip(w, tiles))
+            threads = rc.recon_mb_threads(0)
+            C = torch.zeros(threads, dtype=torch.int32, device=Js[0].device)
+            torch.cuda.synchronize()
+            for _ in range(2):   # the first launch is a warm-up
+                st, mb_ms = rc.recon_mb_atomic(C.data_ptr(), 3, 1024)
+                rc.check(st, "recon_mb_atomic")
+            peak = threads * 1024 / (mb_ms / 1e3)
+            rate = checks / (kms / 1e3)
+            res.update({"bound": "shared-memory atomics", "achieved_Gops": round(rate / 1e9, 2),
+                        "peak_Gops": round(peak / 1e9, 1), "frac": round(rate / peak, 5),
+                        "unit_op": "one neighbour test / compare-and-swap per neighbour of a popped entry"})
+        out[name] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -583,6 +626,8 @@ def main():
     compare = None
     if args.compare and len(tiles) > 1:
         compare = compare_schedules(rc, ctx, stream, Is, Js, J0, tiles, desc, px, flush, args)
+        if args.op == "dilate":
+            compare["phases"] = phase_rooflines(rc, ctx, stream, Js, J0, desc, tiles, px, flush)
 
     # end to end: host (pinned) buffers through recon_batch_host
     Jh = [x.clone().pin_memory() for x in Js_h]

@@ -50,6 +50,7 @@ struct Smem {
     unsigned pairmask[BH / 32];   // rows changed by the latest scan pair
     unsigned cq[3];               // level sizes, rotating by level (see run_queue)
     unsigned item, tile, flag, overflow, notify, visited;
+    unsigned rpops;               // entries the per-warp rings processed since the seeding
     unsigned phase;               // parity of the TMA barrier's next completion
     unsigned abrt;                // block-uniform copy of the abort word
     Work acc;                     // thread 0: counters of consecutive visits to tile acc_tile
@@ -560,7 +561,7 @@ __device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp, const unsigned *filter
 #pragma unroll
     for (int i = 0; i < BH / 32; ++i) rm[i] = filter ? filter[i] : 0u;
     __syncthreads();
-    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; }
+    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; S.rpops = 0; }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = lane + W0;
     for (int y = 1 + (threadIdx.x >> 5); y <= BH; y += NT / 32) {
@@ -623,7 +624,7 @@ __device__ unsigned seed_frame(Smem<BH> &S, uint16_t *gsp)
 {
     constexpr int RB = PW * 4;
     constexpr int NFR = 2 * BW + 2 * (BH - 2);
-    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; }
+    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; S.rpops = 0; }
     __syncthreads();
     const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
     const uint8_t *Ib = (const uint8_t *)S.I;
@@ -794,6 +795,7 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
             __syncwarp();
             unsigned head = 0, tail = hi - lo;
             long batches = 0;
+            unsigned wpops = 0;   // this warp's ring entries
             while (head < tail) {
                 if (++batches > MAX_LEVELS) {
                     if (lane == 0) set_abort(P, AB_LEVELS);
@@ -826,11 +828,13 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
                     S.overflow = 1;
                 }
                 head += m;
-                pops += m;
+                wpops += m;
                 ++nlevels;
                 __syncwarp();
             }
+            if (lane == 0 && wpops) atomicAdd(&S.rpops, wpops);
             __syncthreads();
+            pops += S.rpops;   // every warp's entries, the same in every thread
             break;
         }
         const unsigned navail = min(n, (unsigned)(QCAP + GCAP));
