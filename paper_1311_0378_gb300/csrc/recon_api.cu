@@ -602,6 +602,16 @@ extern "C" int recon_last_kernel_ms(recon_ctx *c, float *ms)
 // ---------------------------------------------------------------------------
 // end-to-end entry points (host buffers)
 
+// Rows of `width` bytes between host and device: one linear copy when both
+// sides are contiguous, a 2-D copy otherwise.
+static cudaError_t copy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t height,
+                             cudaMemcpyKind kind, cudaStream_t st)
+{
+    if (dpitch == width && spitch == width)
+        return cudaMemcpyAsync(dst, src, width * height, kind, st);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, st);
+}
+
 extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
 {
     if (!c || !tiles || n < 1) return RECON_EINVAL;
@@ -624,9 +634,9 @@ extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
     for (int t = 0; t < n; ++t) {
         const recon_tile &T = tiles[t];
         uint8_t *dI = c->d_img + off[t], *dJ = c->d_img + total + off[t];
-        CK(cudaMemcpy2DAsync(dI, T.W, T.I, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
+        CK(copy_rows(dI, T.W, T.I, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
         if (T.op != RECON_OP_FILL_HOLES)   // a FillHoles tile's J is output only
-            CK(cudaMemcpy2DAsync(dJ, T.W, T.J, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
+            CK(copy_rows(dJ, T.W, T.J, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
         dt[t] = T;
         dt[t].I = dI; dt[t].J = dJ; dt[t].pitch = T.W;
     }
@@ -637,7 +647,7 @@ extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
     if (rc) { cudaStreamSynchronize(c->stream); return rc; }
     for (int t = 0; t < n; ++t) {
         const recon_tile &T = tiles[t];
-        CK(cudaMemcpy2DAsync(T.J, T.pitch, dt[t].J, T.W, T.W, T.H, cudaMemcpyDeviceToHost, c->stream));
+        CK(copy_rows(T.J, T.pitch, dt[t].J, T.W, T.W, T.H, cudaMemcpyDeviceToHost, c->stream));
     }
     return recon_sync(c);
 }
