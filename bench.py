@@ -381,7 +381,8 @@ def run_dt(args):
     w, tiles, _ = workload_tiles(args.workload)
     masks = dt_masks(w, tiles[:8])
     px = sum(m.size for m in masks)
-    ctx = rc.recon_init(0, 0, 0)
+    # the transform runs on torch's current stream, where the timing events are recorded
+    ctx = rc.recon_init(0, torch.cuda.current_stream().cuda_stream, 0)
     dB = [torch.from_numpy(m).cuda() for m in masks]
     d2 = [torch.empty(m.shape, dtype=torch.int32, device="cuda") for m in masks]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
