@@ -41,12 +41,26 @@ OP_CODE = {"dilate": 0, "erode": 1, "fill_holes": 2}
 OPS = sorted(list(OP_CODE) + ["dt"])
 
 
-def kernel_hash():
+def code_of(text):
+    """Source text without comments and blank space: what the compiler sees of it."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(l.strip() for l in text.splitlines() if l.strip())
+
+
+def kernel_hash(read=None):
+    """Hash of the reconstruction kernel's code (comments excluded), to tell
+    whether committed ncu counters still describe it."""
     import hashlib
     h = hashlib.sha256()
     for f in ("paper_1311_0378_gb300/csrc/recon_kernels.cu", "paper_1311_0378_gb300/csrc/recon_internal.h"):
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        if read:
+            text = read(f)
+        else:
+            with open(os.path.join(ROOT, f)) as fh:
+                text = fh.read()
+        h.update(code_of(text).encode())
     return h.hexdigest()[:16]
 
 

@@ -7,14 +7,20 @@
 // order (the "cold" list), then blocks re-queued because a neighbour raised a
 // pixel on their border (a ring in global memory). A CTA reconstructs its block
 // locally in shared memory against the block's 1-pixel halo:
-//   1. k raster + anti-raster scan pairs (each scan row is one warp: a vertical
-//      max from the previous row, then a warp prefix scan of clamp maps along
-//      the row), or scans until a pair changes nothing (variant k < 0);
+//   1. k raster + anti-raster scan pairs, then (adaptive variants) more pairs
+//      while a pair still raises enough pixels, or scans until a pair changes
+//      nothing (variant k < 0). Up to four warps scan row bands at once; a
+//      scan row is one warp: a vertical max from the previous row, then a warp
+//      prefix scan of clamp maps along the row, in two-plane u16x2 arithmetic;
 //   2. a seeding pass: one in-place geodesic dilation whose changed pixels form
-//      the frontier (Algorithm 1's initialization phase);
-//   3. the wavefront phase: level-synchronous queue processing in shared
-//      memory (warp-ballot compaction, spill to global memory), each update an
-//      atomic byte max under the mask, J(q) <- max(J(q), min(J(p), I(q))).
+//      the frontier (Algorithm 1's initialization phase) -- after scans only
+//      next to the rows the last pair changed, on revisits only on the frame;
+//   3. the wavefront phase in shared memory: wide levels level-synchronously
+//      (warp-ballot compaction, spill to global memory), thin ones in per-warp
+//      rings; each update an atomic byte max under the mask,
+//      J(q) <- max(J(q), min(J(p), I(q))).
+// Erosion tiles run the same steps on complemented values (complemented as
+// they are loaded and stored).
 // The block then writes its changed rows and notifies each neighbour block
 // whose halo can now receive a propagation. Every update is a monotone step
 // towards the unique fixed point R, so any order of blocks and updates yields
