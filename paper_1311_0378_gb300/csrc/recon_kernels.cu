@@ -279,10 +279,16 @@ __device__ void load_block(Smem<BH> &S, const TileDesc &D, int y0, int x0, bool 
     const int H = D.H, W = D.W;
     const size_t pitch = (size_t)D.pitch;
     constexpr int NW = WR - WL + 1;   // 34 words per row: halo, 32 interior, halo
-    for (int idx = threadIdx.x; idx < (BH + 2) * NW; idx += NT) {
-        const int r = idx / NW, w = WL + (idx - r * NW);
+    // halo_only: the two halo rows, then the left and right halo words of rows 1..BH
+    const int nitems = halo_only ? 2 * NW + 2 * BH : (BH + 2) * NW;
+    for (int idx = threadIdx.x; idx < nitems; idx += NT) {
+        int r, w;
+        if (!halo_only) { r = idx / NW; w = WL + (idx - r * NW); }
+        else if (idx < NW) { r = 0; w = WL + idx; }
+        else if (idx < 2 * NW) { r = BH + 1; w = WL + (idx - NW); }
+        else if (idx < 2 * NW + BH) { r = 1 + (idx - 2 * NW); w = WL; }
+        else { r = 1 + (idx - 2 * NW - BH); w = WR; }
         const bool hrow = (r == 0 || r == BH + 1), hword = (w == WL || w == WR);
-        if (halo_only && !hrow && !hword) continue;
         const int yy = y0 - 1 + r;
         uint32_t jv = 0, iv = 0, loaded = 0;   // loaded: the bytes read from the image
         const bool rowin = (yy >= 0 && yy < H);
