@@ -253,6 +253,19 @@ int recon_mlp_adam(recon_ctx *ctx, float *theta, float *grad, float *m, float *v
 int recon_mlp_train(recon_ctx *ctx, float *theta, const float *X, const float *T, int n, int epochs,
                     int batch, float lr, uint64_t seed, float *epoch_loss);
 
+/* Resumable form of recon_mlp_train (checkpoint / resume of the cost model's
+ * training). adam_mv: DEVICE, 2 * RECON_MLP_NPARAMS floats, Adam's first then
+ * second moment estimates (zeros to start). *step (HOST, in/out): Adam steps
+ * taken so far (0 to start). epoch0: index of the first epoch to run; the
+ * mini-batch shuffle of epoch e depends only on (seed, e), so running epochs
+ * [0, a) and then, from the saved theta / adam_mv / step, [a, a + b) follows
+ * the same sequence of updates as running [0, a + b) at once (up to the
+ * summation order of the gradient reduction). Other arguments as in
+ * recon_mlp_train; epoch_loss receives `epochs` values. Syncs. */
+int recon_mlp_train_resume(recon_ctx *ctx, float *theta, float *adam_mv, int *step, int epoch0,
+                           const float *X, const float *T, int n, int epochs, int batch, float lr,
+                           uint64_t seed, float *epoch_loss);
+
 /* Installs a trained model for RECON_FLAG_LEARNED batches. theta and norm are
  * HOST pointers: norm = (mean_a, std_a, mean_b, std_b) de-normalising the two
  * outputs; variant_a / variant_b are the variants (as in recon_batch_ex) that

@@ -31,7 +31,8 @@ SYMBOLS = ("recon_init", "recon_run", "recon_run_op", "recon_batch", "recon_batc
            "recon_last_kernel_ms", "recon_features", "recon_mlp_forward", "recon_mlp_grad",
            "recon_mlp_adam", "recon_mlp_train", "recon_sched_set_model", "recon_sched_plan_batch",
            "recon_autotune", "recon_sync_for", "recon_trace", "recon_run_noalloc",
-           "recon_mb_threads", "recon_mb_random", "recon_mb_atomic", "recon_dt", "recon_dt_levels")
+           "recon_mb_threads", "recon_mb_random", "recon_mb_atomic", "recon_dt", "recon_dt_levels",
+           "recon_mlp_train_resume")
 RECON_NFEAT, RECON_MLP_NPARAMS = 20, 5634
 
 
@@ -98,6 +99,7 @@ def lib() -> ctypes.CDLL:
         "recon_mb_threads": ([i], i),
         "recon_dt": ([vp, vp, vp, vp, i, i], i),
         "recon_dt_levels": ([vp], i),
+        "recon_mlp_train_resume": ([vp, vp, vp, ip, i, vp, vp, i, i, i, ctypes.c_float, ctypes.c_uint64, vp], i),
         "recon_mb_random": ([vp, i, ctypes.c_uint64, i, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_float)], i),
         "recon_mb_atomic": ([vp, i, i, ctypes.POINTER(ctypes.c_float)], i),
@@ -232,6 +234,16 @@ def recon_mlp_train(ctx, theta: int, X: int, T: int, n: int, epochs: int, batch:
     losses = (ctypes.c_float * epochs)()
     rc = lib().recon_mlp_train(ctx, theta, X, T, n, epochs, batch, lr, seed, losses)
     return rc, list(losses)
+
+
+def recon_mlp_train_resume(ctx, theta: int, adam_mv: int, step: int, epoch0: int, X: int, T: int, n: int,
+                           epochs: int, batch: int, lr: float, seed: int = 0):
+    """Returns (status, step after training, [mean batch loss per epoch])."""
+    losses = (ctypes.c_float * epochs)()
+    st = ctypes.c_int(step)
+    rc = lib().recon_mlp_train_resume(ctx, theta, adam_mv, ctypes.byref(st), epoch0, X, T, n, epochs, batch, lr,
+                                      seed, losses)
+    return rc, st.value, list(losses)
 
 
 def recon_sched_set_model(ctx, theta_host: Sequence[float], norm: Sequence[float], variant_a: int,

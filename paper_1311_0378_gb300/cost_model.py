@@ -58,6 +58,78 @@ def load(path: str = MODEL_PATH):
     return theta, norm, (va, vb), meta
 
 
+CKPT_MAGIC = b"RCK1"
+
+
+def save_checkpoint(path: str, theta: np.ndarray, adam_mv: np.ndarray, state: dict) -> None:
+    """Training checkpoint: magic, header length, a JSON header (state: step,
+    epoch, norm, seed, lr, batch, variants, ...), then theta and Adam's two
+    moment vectors as flat fp32. Written to a temporary file, then renamed."""
+    head = json.dumps(state).encode()
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        f.write(CKPT_MAGIC)
+        f.write(struct.pack("<i", len(head)))
+        f.write(head)
+        f.write(np.asarray(theta, np.float32).tobytes())
+        f.write(np.asarray(adam_mv, np.float32).tobytes())
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str):
+    """Returns (theta, adam_mv, state) of a checkpoint written by save_checkpoint."""
+    n = rc.RECON_MLP_NPARAMS
+    with open(path, "rb") as f:
+        if f.read(4) != CKPT_MAGIC:
+            raise ValueError("not a cost-model training checkpoint: " + path)
+        (nh,) = struct.unpack("<i", f.read(4))
+        state = json.loads(f.read(nh).decode())
+        theta = np.frombuffer(f.read(4 * n), np.float32).copy()
+        mv = np.frombuffer(f.read(8 * n), np.float32).copy()
+    if theta.size != n or mv.size != 2 * n:
+        raise ValueError("truncated checkpoint: " + path)
+    return theta, mv, state
+
+
+def train_resumable(ctx, X: np.ndarray, Y: np.ndarray, epochs=200, batch=256, lr=2e-3, seed=0,
+                    checkpoint: str = None, every: int = 50, resume: str = None):
+    """GPU training with checkpoints every `every` epochs (and at the end) to
+    `checkpoint`; `resume` continues from a checkpoint (its theta, Adam state,
+    step, epoch and output normalisation). Returns (theta, norm, losses of the
+    epochs run here)."""
+    import torch
+    if resume:
+        theta, mv, state = load_checkpoint(resume)
+        norm, step, epoch0 = state["norm"], state["step"], state["epoch"]
+        seed, lr, batch = state["seed"], state["lr"], state["batch"]
+    else:
+        mean, std = Y.mean(axis=0), Y.std(axis=0) + 1e-6
+        norm = [float(mean[0]), float(std[0]), float(mean[1]), float(std[1])]
+        theta = init_params(np.random.default_rng(seed))
+        mv = np.zeros(2 * rc.RECON_MLP_NPARAMS, np.float32)
+        step, epoch0 = 0, 0
+    T = (Y - np.array([norm[0], norm[2]])) / np.array([norm[1], norm[3]])
+    dth = torch.from_numpy(np.ascontiguousarray(theta)).cuda()
+    dmv = torch.from_numpy(np.ascontiguousarray(mv)).cuda()
+    dX = torch.from_numpy(X.astype(np.float32)).cuda()
+    dT = torch.from_numpy(T.astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    losses = []
+    epoch = epoch0
+    while epoch < epochs:
+        k = min(every if every > 0 else epochs, epochs - epoch)
+        st, step, ls = rc.recon_mlp_train_resume(ctx, dth.data_ptr(), dmv.data_ptr(), step, epoch, dX.data_ptr(),
+                                                 dT.data_ptr(), len(X), k, batch, lr, seed)
+        rc.check(st, "recon_mlp_train_resume")
+        epoch += k
+        losses += ls
+        if checkpoint:
+            save_checkpoint(checkpoint, dth.cpu().numpy(), dmv.cpu().numpy(),
+                            {"step": step, "epoch": epoch, "epochs": epochs, "norm": norm, "seed": seed,
+                             "lr": lr, "batch": batch, "samples": int(len(X))})
+    return dth.cpu().numpy(), norm, losses
+
+
 def install(ctx, path: str = MODEL_PATH) -> dict:
     theta, norm, (va, vb), meta = load(path)
     rc.check(rc.recon_sched_set_model(ctx, theta, norm, va, vb), "recon_sched_set_model")
@@ -215,6 +287,10 @@ def main():
                     help="variant A: 1 scan pair, then keep scanning while a pair raises >= 512 px")
     ap.add_argument("--eval", action="store_true", help="then compare learned vs plain on eval1000")
     ap.add_argument("--eval-only", action="store_true", help="only evaluate the model at --out")
+    ap.add_argument("--data", help="reuse a labelled dataset (.npz written by an earlier run) instead of labelling")
+    ap.add_argument("--checkpoint", help="write a training checkpoint here every --checkpoint-every epochs")
+    ap.add_argument("--checkpoint-every", type=int, default=50)
+    ap.add_argument("--resume", help="continue training from this checkpoint")
     args = ap.parse_args()
     w = synth.workload("train20k")
     specs = list(w.tiles[:args.tiles])
@@ -225,17 +301,27 @@ def main():
         return
     variants = (args.scan_variant, args.queue_k)
     t0 = time.time()
-    X, Y, Yms = build_dataset(ctx, specs, w.seed, variants)
+    if args.data:
+        d = np.load(args.data)
+        X, Y, Yms = d["X"], d["Y"], d["Yms"]
+    else:
+        X, Y, Yms = build_dataset(ctx, specs, w.seed, variants)
     t1 = time.time()
-    theta, norm, losses = train(ctx, X, Y, epochs=args.epochs)
+    if args.checkpoint or args.resume:
+        theta, norm, losses = train_resumable(ctx, X, Y, epochs=args.epochs, checkpoint=args.checkpoint,
+                                              every=args.checkpoint_every, resume=args.resume)
+    else:
+        theta, norm, losses = train(ctx, X, Y, epochs=args.epochs)
     t2 = time.time()
     pick_b = float(np.mean(Y[:, 1] < Y[:, 0]))
     meta = {"tiles": len(specs), "workload": w.name, "seed": w.seed, "variants": list(variants),
             "label": "log CTA-busy milliseconds (work) of the tile reconstructed alone", "epochs": args.epochs,
-            "final_loss": losses[-1], "first_loss": losses[0], "label_seconds": round(t1 - t0, 1),
+            "final_loss": losses[-1] if losses else None, "first_loss": losses[0] if losses else None,
+            "label_seconds": round(t1 - t0, 1),
             "train_seconds": round(t2 - t1, 1), "fraction_b_faster": pick_b}
     save(args.out, theta, norm, variants, meta)
-    np.savez_compressed(os.path.splitext(args.out)[0] + "_data.npz", X=X, Y=Y, Yms=Yms)
+    if not args.data:
+        np.savez_compressed(os.path.splitext(args.out)[0] + "_data.npz", X=X, Y=Y, Yms=Yms)
     print(json.dumps(meta), flush=True)
     if args.eval:
         print(json.dumps(evaluate(ctx, args.out)), flush=True)

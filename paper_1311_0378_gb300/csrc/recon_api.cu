@@ -719,24 +719,27 @@ static uint64_t sm64(uint64_t z)
     return z ^ (z >> 31);
 }
 
-extern "C" int recon_mlp_train(recon_ctx *c, float *theta, const float *X, const float *T, int n, int epochs,
-                               int batch, float lr, uint64_t seed, float *epoch_loss)
+extern "C" int recon_mlp_train_resume(recon_ctx *c, float *theta, float *adam_mv, int *step, int epoch0,
+                                      const float *X, const float *T, int n, int epochs, int batch, float lr,
+                                      uint64_t seed, float *epoch_loss)
 {
-    if (!c || !theta || !X || !T || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0f)) return RECON_EINVAL;
+    if (!c || !theta || !adam_mv || !step || *step < 0 || epoch0 < 0 || !X || !T || n < 1 || epochs < 1 ||
+        batch < 1 || !(lr > 0.0f))
+        return RECON_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
-    float *m = nullptr, *v = nullptr, *g = nullptr, *dl = nullptr;
+    float *m = adam_mv, *v = adam_mv + MLP_NPARAMS, *g = nullptr, *dl = nullptr;
     int *didx = nullptr;
-    cudaError_t e = cudaMalloc((void **)&m, sizeof(float) * MLP_NPARAMS * 3);
-    if (e == cudaSuccess) { v = m + MLP_NPARAMS; g = v + MLP_NPARAMS; }
-    if (e == cudaSuccess) e = cudaMemsetAsync(m, 0, sizeof(float) * MLP_NPARAMS * 3, c->stream);
+    cudaError_t e = cudaMalloc((void **)&g, sizeof(float) * MLP_NPARAMS);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g, 0, sizeof(float) * MLP_NPARAMS, c->stream);
     if (e == cudaSuccess) e = cudaMalloc((void **)&didx, sizeof(int) * (size_t)n * 2);
     if (e == cudaSuccess) e = cudaMalloc((void **)&dl, sizeof(float) * epochs);
     if (e == cudaSuccess) e = cudaMemsetAsync(dl, 0, sizeof(float) * epochs, c->stream);
     std::vector<int> perm(n);
-    int t = 0;
+    int t = *step;
     const int nbatches = (n + batch - 1) / batch;
-    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+    for (int k = 0; k < epochs && e == cudaSuccess; ++k) {
+        const int ep = epoch0 + k;   // the shuffle depends on the absolute epoch, so a resumed run repeats it
         // Fisher-Yates shuffle driven by SplitMix64 outputs of (seed, epoch)
         for (int i = 0; i < n; ++i) perm[i] = i;
         uint64_t st = sm64(seed ^ sm64((uint64_t)ep + 1));
@@ -745,12 +748,12 @@ extern "C" int recon_mlp_train(recon_ctx *c, float *theta, const float *X, const
             const int j = (int)(st % (uint64_t)(i + 1));
             std::swap(perm[i], perm[j]);
         }
-        int *buf = didx + (size_t)(ep & 1) * n;  // double-buffered: the copy of epoch e+1 cannot race epoch e
+        int *buf = didx + (size_t)(k & 1) * n;  // double-buffered: the copy of epoch e+1 cannot race epoch e
         e = cudaMemcpyAsync(buf, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // perm is pageable and reused
         for (int s = 0; s < n && e == cudaSuccess; s += batch) {
             const int nb = std::min(batch, n - s);
-            e = rl_grad(theta, X, T, buf + s, nb, g, dl + ep, c->stream);
+            e = rl_grad(theta, X, T, buf + s, nb, g, dl + k, c->stream);
             if (e == cudaSuccess) e = rl_adam(theta, g, m, v, ++t, lr, c->stream);
         }
     }
@@ -760,10 +763,27 @@ extern "C" int recon_mlp_train(recon_ctx *c, float *theta, const float *X, const
         for (int i = 0; i < epochs; ++i) epoch_loss[i] /= (float)nbatches;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(m);
+    if (e == cudaSuccess) *step = t;
+    cudaFree(g);
     cudaFree(didx);
     cudaFree(dl);
     return cuda_status(e);
+}
+
+extern "C" int recon_mlp_train(recon_ctx *c, float *theta, const float *X, const float *T, int n, int epochs,
+                               int batch, float lr, uint64_t seed, float *epoch_loss)
+{
+    if (!c) return RECON_EINVAL;
+    CK(cudaSetDevice(c->device));
+    float *mv = nullptr;
+    CK(cudaMalloc((void **)&mv, sizeof(float) * MLP_NPARAMS * 2));
+    int step = 0;
+    cudaError_t e = cudaMemsetAsync(mv, 0, sizeof(float) * MLP_NPARAMS * 2, c->stream);
+    int rc = e == cudaSuccess ? recon_mlp_train_resume(c, theta, mv, &step, 0, X, T, n, epochs, batch, lr, seed,
+                                                       epoch_loss)
+                              : cuda_status(e);
+    cudaFree(mv);
+    return rc;
 }
 
 extern "C" int recon_sched_set_model(recon_ctx *c, const float *theta, const float *norm, int variant_a,

@@ -26,3 +26,28 @@ def test_init_params_layout():
     th = cost_model.init_params(np.random.default_rng(0))
     assert th.dtype == np.float32 and th.size == rc.RECON_MLP_NPARAMS
     assert np.all(th[20 * 64:20 * 64 + 64] == 0)   # b1 starts at zero
+
+
+def test_checkpoint_roundtrip(tmp_path):
+    n = rc.RECON_MLP_NPARAMS
+    theta = np.linspace(-1, 1, n, dtype=np.float32)
+    mv = np.arange(2 * n, dtype=np.float32) * 1e-3
+    state = {"step": 123, "epoch": 4, "norm": [0.5, 2.0, 1.5, 3.0], "seed": 9, "lr": 2e-3, "batch": 256}
+    p = tmp_path / "c.ckpt"
+    cost_model.save_checkpoint(str(p), theta, mv, state)
+    th, m2, st = cost_model.load_checkpoint(str(p))
+    assert np.array_equal(th, theta) and np.array_equal(m2, mv) and st == state
+    assert not (tmp_path / "c.ckpt.tmp").exists()
+
+
+def test_checkpoint_rejects_bad_and_truncated(tmp_path):
+    p = tmp_path / "bad.ckpt"
+    p.write_bytes(b"RCM1" + b"\0" * 64)
+    with pytest.raises(ValueError):
+        cost_model.load_checkpoint(str(p))
+    q = tmp_path / "short.ckpt"
+    cost_model.save_checkpoint(str(q), np.zeros(rc.RECON_MLP_NPARAMS, np.float32),
+                               np.zeros(2 * rc.RECON_MLP_NPARAMS, np.float32), {"step": 0})
+    q.write_bytes(q.read_bytes()[:-100])
+    with pytest.raises(ValueError):
+        cost_model.load_checkpoint(str(q))

@@ -129,3 +129,38 @@ def test_training_reduces_loss_like_oracle(ctx):
     l_cpu = mlp.loss(mlp.forward(mlp.train(theta0, X, T, 40, 3e-3, 64, 1), X)[0], T)
     assert l_gpu < 0.05 * l0 and l_cpu < 0.05 * l0
     assert losses[-1] < losses[0]
+
+
+def test_training_checkpoint_resume(ctx, tmp_path):
+    """Training 3 epochs, checkpointing (theta, Adam moments, step, epoch) to a
+    file and resuming for 3 more follows the same update sequence as 6 epochs
+    at once (the shuffle of epoch e depends only on (seed, e)); the two end
+    points agree up to the summation order of the gradient reduction."""
+    from paper_1311_0378_gb300 import cost_model
+    rng = np.random.default_rng(8)
+    n = 1500
+    X = rng.uniform(0, 1, size=(n, 20))
+    T = np.stack([X[:, :4].sum(1) - 2.0, X[:, 7] - 0.5], axis=1)
+    theta0 = mlp.init(3)
+    npar = rc.RECON_MLP_NPARAMS
+    dX, dT = f32(X), f32(T)
+    # straight: 6 epochs
+    th_a, mv_a = f32(theta0), f32(np.zeros(2 * npar))
+    st, step_a, _ = rc.recon_mlp_train_resume(ctx, th_a.data_ptr(), mv_a.data_ptr(), 0, 0, dX.data_ptr(),
+                                              dT.data_ptr(), n, 6, 100, 2e-3, 5)
+    rc.check(st, "straight")
+    # 3 epochs, checkpoint through a file, resume 3
+    th_b, mv_b = f32(theta0), f32(np.zeros(2 * npar))
+    st, step_b, _ = rc.recon_mlp_train_resume(ctx, th_b.data_ptr(), mv_b.data_ptr(), 0, 0, dX.data_ptr(),
+                                              dT.data_ptr(), n, 3, 100, 2e-3, 5)
+    rc.check(st, "first half")
+    p = str(tmp_path / "t.ckpt")
+    cost_model.save_checkpoint(p, th_b.cpu().numpy(), mv_b.cpu().numpy(), {"step": step_b, "epoch": 3})
+    th_l, mv_l, state = cost_model.load_checkpoint(p)
+    th_c, mv_c = f32(th_l), f32(mv_l)
+    st, step_c, _ = rc.recon_mlp_train_resume(ctx, th_c.data_ptr(), mv_c.data_ptr(), state["step"],
+                                              state["epoch"], dX.data_ptr(), dT.data_ptr(), n, 3, 100, 2e-3, 5)
+    rc.check(st, "resumed half")
+    assert step_a == step_c == 6 * 15
+    close(th_c.cpu().numpy(), th_a.cpu().numpy(), rtol=1e-3)
+    assert not np.allclose(th_a.cpu().numpy(), theta0)   # it trained
