@@ -79,7 +79,12 @@ static int grow(T **p, size_t *cap, size_t need)
     *p = nullptr;
     *cap = 0;
     size_t n = std::max(need, (size_t)1);
-    CK(cudaMalloc((void **)p, n * sizeof(T)));
+    const cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // an allocation failure leaves the context usable: clear it
+        *p = nullptr;
+        return cuda_status(e);
+    }
     *cap = n;
     return RECON_OK;
 }

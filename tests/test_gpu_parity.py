@@ -246,3 +246,15 @@ def test_single4096_all_runs(ctx):
     want, _ = oracle.recon_tiles(pairs, [s.conn for s in w.tiles], "sweep")
     for (I, J), s, R in zip(pairs, w.tiles, want):
         np.testing.assert_array_equal(gpu_recon(ctx, I, J, s.conn), R)
+
+
+def test_allocation_failure_is_reported_and_context_recovers(fresh_ctx):
+    """A host batch whose device copy cannot fit (about 600 GB) fails with
+    RECON_ENOMEM before any copy or launch (the host buffers are never read),
+    and the same context then reconstructs normally."""
+    small = np.zeros(64, np.uint8)
+    huge = (small.ctypes.data, small.ctypes.data, 550000, 550000, 550000, 8)
+    assert rc.recon_batch_host(fresh_ctx, [huge]) == rc.RECON_ENOMEM
+    spec = synth.workload("single512").tiles[0]
+    I, J = synth.tile_pair(spec, 1)
+    np.testing.assert_array_equal(gpu_recon(fresh_ctx, I, J, 8), oracle.recon(I, J, 8))
