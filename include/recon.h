@@ -153,9 +153,11 @@ enum {
                                 6 notify, 7 ring slot, 8 idle wait, 9 ring push, 10 TMA) */
     RECON_P_REVISIT_SCANS = 11, /* scan pairs a block runs when revisited (after a neighbour
                                    raised its halo) before its queue phase; default 0 */
-    RECON_P_SCAN_GAIN = 12      /* default adaptive scan-to-queue switch: after its fixed scan
+    RECON_P_SCAN_GAIN = 12,     /* default adaptive scan-to-queue switch: after its fixed scan
                                    pairs a block keeps scanning while a pair raises at least this
                                    many pixels (first visits and revisits); 0 = off */
+    RECON_P_TUNE_FROM_CACHE = 13 /* read-only: 1 if the last recon_autotune call took its
+                                   result from the cache instead of timing trials */
 };
 int recon_set_param(recon_ctx *ctx, int key, int64_t value);
 int64_t recon_get_param(recon_ctx *ctx, int key);
@@ -214,6 +216,20 @@ int recon_run_noalloc(const uint8_t *I, uint8_t *J, int H, int W, int conn, void
  * holds its original marker on return. The paper tunes its scan-to-queue
  * switch point the same way (Sec. V-C). */
 int recon_autotune(recon_ctx *ctx, const recon_tile *tiles, int n, int reps, int *best);
+/* The autotuner keeps its results in the context, keyed by the batch's size
+ * bucket (round(log2 of the mean tile area)), its connectivities (bit 0: 4,
+ * bit 1: 8) and its marker class (1 when most marker pixels are 0, as for
+ * border-seeded markers; 0 otherwise). A recon_autotune call on a batch whose
+ * key is cached installs the cached result without timing anything
+ * (RECON_P_TUNE_FROM_CACHE reads 1 afterwards).
+ * recon_autotune_cache copies up to max_entries entries of 7 ints {bucket,
+ * connectivities, marker class, block height, bands, scan pairs, scan gain}
+ * into entries (HOST) and returns how many the cache holds (negative status on
+ * bad arguments). recon_autotune_cache_load adds such entries (count = 0
+ * clears the cache); it validates every entry first and returns RECON_EINVAL,
+ * changing nothing, if one is out of range. Together they persist the cache. */
+int recon_autotune_cache(recon_ctx *ctx, int *entries, int max_entries);
+int recon_autotune_cache_load(recon_ctx *ctx, const int *entries, int count);
 
 /* ---- learned cost model ------------------------------------------------
  * The scheduler's analogue of the paper's performance-aware task scheduling

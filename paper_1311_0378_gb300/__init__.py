@@ -21,7 +21,7 @@ RECON_OK, RECON_EINVAL, RECON_EMARKER, RECON_ENOMEM, RECON_ECUDA, RECON_ETIMEOUT
 RECON_FLAG_SYNC, RECON_FLAG_NO_CHECK, RECON_FLAG_LEARNED, RECON_FLAG_NO_GRAPH = 1, 2, 4, 8
 (RECON_P_BLOCK_H, RECON_P_SWEEPS, RECON_P_GRID, RECON_P_BANDS, RECON_P_WAIT_NS, RECON_P_ORDER,
  RECON_P_TEST_STALL, RECON_P_TMA, RECON_P_TRACE, RECON_P_LAST_ABORT, RECON_P_REVISIT_SCANS,
- RECON_P_SCAN_GAIN) = range(1, 13)
+ RECON_P_SCAN_GAIN, RECON_P_TUNE_FROM_CACHE) = range(1, 14)
 RECON_OP_DILATE, RECON_OP_ERODE, RECON_OP_FILL_HOLES = 0, 1, 2
 
 # every symbol the header declares; tests check the library exports them all
@@ -32,7 +32,7 @@ SYMBOLS = ("recon_init", "recon_run", "recon_run_op", "recon_batch", "recon_batc
            "recon_mlp_adam", "recon_mlp_train", "recon_sched_set_model", "recon_sched_plan_batch",
            "recon_autotune", "recon_sync_for", "recon_trace", "recon_run_noalloc",
            "recon_mb_threads", "recon_mb_random", "recon_mb_atomic", "recon_dt", "recon_dt_levels",
-           "recon_mlp_train_resume")
+           "recon_mlp_train_resume", "recon_autotune_cache", "recon_autotune_cache_load")
 RECON_NFEAT, RECON_MLP_NPARAMS = 20, 5634
 
 
@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
         "recon_mb_threads": ([i], i),
         "recon_dt": ([vp, vp, vp, vp, i, i], i),
         "recon_dt_levels": ([vp], i),
+        "recon_autotune_cache": ([vp, vp, i], i),
+        "recon_autotune_cache_load": ([vp, vp, i], i),
         "recon_mlp_train_resume": ([vp, vp, vp, ip, i, vp, vp, i, i, i, ctypes.c_float, ctypes.c_uint64, vp], i),
         "recon_mb_random": ([vp, i, ctypes.c_uint64, i, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_float)], i),
@@ -268,6 +270,22 @@ def recon_autotune(ctx, tiles, reps: int = 2):
     best = (ctypes.c_int * 4)()
     rc = lib().recon_autotune(ctx, _tiles(tiles), len(tiles), reps, best)
     return rc, tuple(best)
+
+
+def recon_autotune_cache(ctx):
+    """The autotuner's cache: (status, [(bucket, conns, marker_class, bh, bands, k, gain), ...])."""
+    n = lib().recon_autotune_cache(ctx, None, 0)
+    if n < 0:
+        return -n, []
+    buf = (ctypes.c_int * max(7 * n, 1))()
+    m = lib().recon_autotune_cache(ctx, buf, n)
+    return RECON_OK, [tuple(buf[7 * i:7 * i + 7]) for i in range(min(n, m))]
+
+
+def recon_autotune_cache_load(ctx, entries) -> int:
+    flat = [int(x) for e in entries for x in e]
+    buf = (ctypes.c_int * max(len(flat), 1))(*flat)
+    return lib().recon_autotune_cache_load(ctx, buf, len(entries))
 
 
 def recon_sync_for(ctx, timeout_ms: int) -> int:

@@ -6,8 +6,11 @@
 #include <cstring>
 #include <new>
 #include <vector>
+#include <map>
+#include <tuple>
 #include <algorithm>
 #include <time.h>
+#include <cmath>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -60,6 +63,9 @@ struct recon_ctx {
     int *d_dt_site = nullptr; size_t cap_dt_site = 0;
     unsigned *h_dt_cnt = nullptr;
     int dt_levels = 0;
+    // autotuner results: (size bucket, connectivities, marker class) -> {bh, bands, k, gain}
+    std::map<std::tuple<int, int, int>, std::vector<int>> tune_cache;
+    int tune_from_cache = 0;
 };
 
 static int cuda_status(cudaError_t e)
@@ -249,6 +255,7 @@ extern "C" int64_t recon_get_param(recon_ctx *c, int key)
     case RECON_P_REVISIT_SCANS: return c->revisit_scans;
     case RECON_P_SCAN_GAIN: return c->scan_gain;
     case RECON_P_LAST_ABORT: return c->last_abort;
+    case RECON_P_TUNE_FROM_CACHE: return c->tune_from_cache;
     }
     return -1;
 }
@@ -825,6 +832,63 @@ extern "C" int recon_sched_plan_batch(recon_ctx *c, const recon_tile *tiles, int
 // the caller's batch and keeps the fastest. Results never differ (R is unique),
 // only the time does.
 
+// The autotuner's cache key of a batch: size bucket = round(log2(mean tile
+// area)), the set of connectivities (bit 0: 4, bit 1: 8), and the marker
+// class (1 when most of the batch's marker pixels are 0, as for border-seeded
+// markers such as FillHoles; 0 otherwise), from the cost model's feature pass.
+static int tune_key(recon_ctx *c, const recon_tile *tiles, int n, std::tuple<int, int, int> *key)
+{
+    double area = 0.0;
+    int conns = 0;
+    for (int t = 0; t < n; ++t) {
+        area += (double)tiles[t].H * tiles[t].W;
+        conns |= tiles[t].conn == 4 ? 1 : 2;
+    }
+    float *feat = nullptr;
+    CK(cudaMalloc((void **)&feat, sizeof(float) * RECON_NFEAT * (size_t)n));
+    int rc = recon_features(c, tiles, n, feat);
+    std::vector<float> h((size_t)RECON_NFEAT * n);
+    if (rc == RECON_OK && cudaMemcpy(h.data(), feat, sizeof(float) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = RECON_ECUDA;
+    cudaFree(feat);
+    if (rc) return rc;
+    double zero = 0.0;
+    for (int t = 0; t < n; ++t) zero += (double)h[(size_t)t * RECON_NFEAT + 17] * tiles[t].H * tiles[t].W;
+    const int bucket = (int)std::lround(std::log2(std::max(area / n, 1.0)));
+    *key = std::make_tuple(bucket, conns, zero >= 0.5 * area ? 1 : 0);
+    return RECON_OK;
+}
+
+extern "C" int recon_autotune_cache(recon_ctx *c, int *entries, int max_entries)
+{
+    if (!c || max_entries < 0 || (max_entries > 0 && !entries)) return -RECON_EINVAL;
+    int i = 0;
+    for (const auto &kv : c->tune_cache) {
+        if (i >= max_entries) break;
+        int *e = entries + 7 * i++;
+        e[0] = std::get<0>(kv.first); e[1] = std::get<1>(kv.first); e[2] = std::get<2>(kv.first);
+        for (int k = 0; k < 4; ++k) e[3 + k] = kv.second[k];
+    }
+    return (int)c->tune_cache.size();
+}
+
+extern "C" int recon_autotune_cache_load(recon_ctx *c, const int *entries, int count)
+{
+    if (!c || count < 0 || (count > 0 && !entries)) return RECON_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const int *e = entries + 7 * i;
+        if ((e[3] != 32 && e[3] != 64 && e[3] != 128) || (e[4] != 1 && e[4] != 2 && e[4] != 4) || e[5] < -1 ||
+            e[5] > 64 || e[6] < 0 || e[6] > (1 << 20) || e[1] < 1 || e[1] > 3 || (e[2] != 0 && e[2] != 1))
+            return RECON_EINVAL;
+    }
+    if (count == 0) c->tune_cache.clear();
+    for (int i = 0; i < count; ++i) {
+        const int *e = entries + 7 * i;
+        c->tune_cache[std::make_tuple(e[0], e[1], e[2])] = std::vector<int>{e[3], e[4], e[5], e[6]};
+    }
+    return RECON_OK;
+}
+
 extern "C" int recon_autotune(recon_ctx *c, const recon_tile *tiles, int n, int reps, int *best)
 {
     if (!c || !tiles || n < 1 || !best || reps < 1 || reps > 100) return RECON_EINVAL;
@@ -832,6 +896,18 @@ extern "C" int recon_autotune(recon_ctx *c, const recon_tile *tiles, int n, int 
         if (!tile_ok(tiles[t])) return RECON_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
+    std::tuple<int, int, int> key;
+    int krc = tune_key(c, tiles, n, &key);
+    if (krc) return krc;
+    c->tune_from_cache = 0;
+    const auto hit = c->tune_cache.find(key);
+    if (hit != c->tune_cache.end()) {   // this kind of batch was tuned before: no trials
+        c->bh = hit->second[0]; c->bands = hit->second[1]; c->k = hit->second[2]; c->scan_gain = hit->second[3];
+        for (int k = 0; k < 4; ++k) best[k] = hit->second[k];
+        c->tune_from_cache = 1;
+        drop_graph(c);
+        return RECON_OK;
+    }
     // backup of every marker so each trial starts from the same J
     size_t total = 0;
     std::vector<size_t> off(n);
@@ -888,6 +964,7 @@ extern "C" int recon_autotune(recon_ctx *c, const recon_tile *tiles, int n, int 
     }
     c->bh = bb[0]; c->bands = bb[1]; c->k = bb[2]; c->scan_gain = bb[3];
     best[0] = bb[0]; best[1] = bb[1]; best[2] = bb[2]; best[3] = bb[3];
+    c->tune_cache[key] = std::vector<int>{bb[0], bb[1], bb[2], bb[3]};
     return RECON_OK;
 }
 
