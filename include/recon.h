@@ -84,6 +84,10 @@ typedef struct {
 
 /* Creates a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
  * (NULL: the context creates its own non-blocking stream). flags: RECON_FLAG_*.
+ * The environment variables RECON_BLOCK_H, RECON_SWEEPS, RECON_BANDS,
+ * RECON_GRID, RECON_WAIT_NS, RECON_ORDER, RECON_TMA, RECON_REVISIT_SCANS and
+ * RECON_SCAN_GAIN, when set, override the matching RECON_P_* defaults (decimal
+ * integers; an invalid value makes the call return RECON_EINVAL).
  * Returns RECON_OK and *ctx, or an error code with *ctx = NULL. */
 int recon_init(recon_ctx **ctx, int device, void *cuda_stream, unsigned flags);
 

@@ -137,6 +137,23 @@ extern "C" int recon_init(recon_ctx **out, int device, void *cuda_stream, unsign
         return cuda_status(e);
     }
     c->sched = recon_sched_create();
+    // environment overrides of the context defaults (RECON_BLOCK_H=64 ...);
+    // a malformed or out-of-range value fails the call rather than being ignored
+    static const struct { const char *name; int key; } env[] = {
+        {"RECON_BLOCK_H", RECON_P_BLOCK_H}, {"RECON_SWEEPS", RECON_P_SWEEPS}, {"RECON_BANDS", RECON_P_BANDS},
+        {"RECON_GRID", RECON_P_GRID}, {"RECON_WAIT_NS", RECON_P_WAIT_NS}, {"RECON_ORDER", RECON_P_ORDER},
+        {"RECON_TMA", RECON_P_TMA}, {"RECON_REVISIT_SCANS", RECON_P_REVISIT_SCANS},
+        {"RECON_SCAN_GAIN", RECON_P_SCAN_GAIN}};
+    for (const auto &ev : env) {
+        const char *v = getenv(ev.name);
+        if (!v || !*v) continue;
+        char *end = nullptr;
+        const long long x = strtoll(v, &end, 10);
+        if (*end != '\0' || recon_set_param(c, ev.key, (int64_t)x) != RECON_OK) {
+            recon_free(c);
+            return RECON_EINVAL;
+        }
+    }
     *out = c;
     return RECON_OK;
 }

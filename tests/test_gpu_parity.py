@@ -258,3 +258,21 @@ def test_allocation_failure_is_reported_and_context_recovers(fresh_ctx):
     spec = synth.workload("single512").tiles[0]
     I, J = synth.tile_pair(spec, 1)
     np.testing.assert_array_equal(gpu_recon(fresh_ctx, I, J, 8), oracle.recon(I, J, 8))
+
+
+def test_environment_overrides():
+    """RECON_* environment variables set the context defaults; a bad value
+    fails recon_init (checked in a child process with its own environment)."""
+    import os
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r); import paper_1311_0378_gb300 as rc\n"
+            "try:\n    c = rc.recon_init(0, 0, 0)\nexcept rc.ReconError as e:\n    print('status', e.status); sys.exit(0)\n"
+            "print(rc.recon_get_param(c, rc.RECON_P_BLOCK_H), rc.recon_get_param(c, rc.RECON_P_SCAN_GAIN))\n"
+            "rc.recon_free(c)\n" % os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    env = dict(os.environ, RECON_BLOCK_H="32", RECON_SCAN_GAIN="256")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120).stdout
+    assert out.split() == ["32", "256"]
+    env["RECON_BLOCK_H"] = "96"
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120).stdout
+    assert out.split() == ["status", str(rc.RECON_EINVAL)]
