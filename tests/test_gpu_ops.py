@@ -189,3 +189,16 @@ def test_host_entry_point_fill_holes():
     finally:
         rc.recon_free(c)
     np.testing.assert_array_equal(J, oracle.fill_holes(I, 4))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_full_size_4096(ctx, conn):
+    """The 4096^2 mask of the bench workload at full size: FillHoles, and the
+    erosion of its complemented fill-holes pair, byte for byte."""
+    reset(ctx)
+    w = synth.workload("single4096")
+    spec = [t for t in w.tiles if t.marker == synth.FILLHOLES and t.conn == conn][0]
+    I, J = synth.tile_pair(spec, w.seed)
+    np.testing.assert_array_equal(gpu_op(ctx, I, None, conn, FILL), oracle.fill_holes(I, conn))
+    Ic, Jc = 255 - I, 255 - J
+    np.testing.assert_array_equal(gpu_op(ctx, Ic, Jc, conn, ERODE), oracle.recon_erode(Ic, Jc, conn))
