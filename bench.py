@@ -87,12 +87,18 @@ def peaks():
 
 
 class Clocks:
-    """Samples SM clock and throttle reasons with nvidia-smi while running."""
+    """Samples SM clock and throttle reasons with nvidia-smi during the timed
+    region: the sampler is started, and its first sample awaited, before the
+    region begins, so the samples taken inside it are counted from there."""
+
+    INTERVAL_MS = 50
 
     def __init__(self, index=0):
         self.index = index
         self.rows = []
         self.proc = None
+        self.start = 0
+        self.end = None
 
     def __enter__(self):
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -100,12 +106,16 @@ class Clocks:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0:   # sampler live before the region starts
+                time.sleep(0.01)
         except OSError:
             self.proc = None
+        self.start = len(self.rows)
         return self
 
     def _read(self):
@@ -115,7 +125,13 @@ class Clocks:
                 self.rows.append(parts)
 
     def __exit__(self, *a):
+        self.end = len(self.rows)
         if self.proc:
+            if self.end == self.start:   # a region shorter than the interval: take the next sample
+                t0 = time.time()
+                while len(self.rows) == self.start and time.time() - t0 < 1.0:
+                    time.sleep(0.005)
+                self.end = len(self.rows)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -123,14 +139,15 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
-        if not self.rows:
+        rows = self.rows[self.start:self.end]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows), "interval_ms": self.INTERVAL_MS}
 
 
 def workload_tiles(name, op="dilate"):
