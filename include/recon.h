@@ -298,6 +298,16 @@ int recon_sched_set_model(recon_ctx *ctx, const float *theta, const float *norm,
 int recon_sched_plan_batch(recon_ctx *ctx, const recon_tile *tiles, int n, int *variant, int *order,
                            float *pred);
 
+/* Bounds-checked build (librecon_checks.so, built with RECON_CHECKS): the
+ * reconstruction kernel checks every wavefront queue slot and pixel offset
+ * before using it, counts failed checks and skips those accesses instead of
+ * making them (the stand-in for a memory checker). recon_checks reports
+ * *enabled (1 in that build, 0 otherwise), the number of failed checks since
+ * the last reset and the where-code of the first (1: queue slot, 2: wavefront
+ * pixel, 3: pushed pixel); reset != 0 clears them. Returns 0, or nonzero on
+ * bad arguments or a CUDA error. */
+int recon_checks(int *enabled, unsigned *violations, unsigned *first, int reset);
+
 /* ---- distance transform (Table II) ----
  * For each foreground pixel (B != 0) of the H x W image B (device uint8,
  * pitch = W), the squared Euclidean distance to the background pixel that the

@@ -32,7 +32,7 @@ SYMBOLS = ("recon_init", "recon_run", "recon_run_op", "recon_batch", "recon_batc
            "recon_mlp_adam", "recon_mlp_train", "recon_sched_set_model", "recon_sched_plan_batch",
            "recon_autotune", "recon_sync_for", "recon_trace", "recon_run_noalloc",
            "recon_mb_threads", "recon_mb_random", "recon_mb_atomic", "recon_dt", "recon_dt_levels",
-           "recon_mlp_train_resume", "recon_autotune_cache", "recon_autotune_cache_load")
+           "recon_mlp_train_resume", "recon_autotune_cache", "recon_autotune_cache_load", "recon_checks")
 RECON_NFEAT, RECON_MLP_NPARAMS = 20, 5634
 
 
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
         "recon_dt": ([vp, vp, vp, vp, i, i], i),
         "recon_dt_levels": ([vp], i),
         "recon_autotune_cache": ([vp, vp, i], i),
+        "recon_checks": ([vp, vp, vp, i], i),
         "recon_autotune_cache_load": ([vp, vp, i], i),
         "recon_mlp_train_resume": ([vp, vp, vp, ip, i, vp, vp, i, i, i, ctypes.c_float, ctypes.c_uint64, vp], i),
         "recon_mb_random": ([vp, i, ctypes.c_uint64, i, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
@@ -286,6 +287,15 @@ def recon_autotune_cache_load(ctx, entries) -> int:
     flat = [int(x) for e in entries for x in e]
     buf = (ctypes.c_int * max(len(flat), 1))(*flat)
     return lib().recon_autotune_cache_load(ctx, buf, len(entries))
+
+
+def recon_checks(reset: bool = False):
+    """(enabled, failed checks, where-code of the first) of the bounds-checked build."""
+    en, viol, first = ctypes.c_int(0), ctypes.c_uint(0), ctypes.c_uint(0)
+    st = lib().recon_checks(ctypes.byref(en), ctypes.byref(viol), ctypes.byref(first), 1 if reset else 0)
+    if st != 0:
+        raise ReconError(RECON_ECUDA, "recon_checks")
+    return en.value, viol.value, first.value
 
 
 def recon_sync_for(ctx, timeout_ms: int) -> int:

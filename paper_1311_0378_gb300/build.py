@@ -30,16 +30,24 @@ def _deps() -> list:
     return hdrs + [os.path.join(ROOT, "include", "recon.h")]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+LIB_CHECKS = os.path.join(PKG, "librecon_checks.so")
+
+
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    """Builds librecon.so; checks=True builds the bounds-checked variant
+    librecon_checks.so instead (-DRECON_CHECKS, see recon_checks in recon.h)."""
+    bdir = BUILD + ("_checks" if checks else "")
+    lib_path = LIB_CHECKS if checks else LIB
+    extra = ["-DRECON_CHECKS"] if checks else []
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     dep_mtime = max(os.path.getmtime(p) for p in _deps())
 
     def compile_one(src: str) -> str:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), dep_mtime):
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o + ".tmp"]
+            cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o + ".tmp"]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             subprocess.check_call(cmd)
@@ -48,11 +56,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -35,6 +35,25 @@ namespace rk {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
+// Bounds-checked build (-DRECON_CHECKS, librecon_checks.so): the stand-in for
+// a memory checker. Every queue slot and every wavefront pixel offset is
+// checked before it is used; a failed check is counted, its where-code kept
+// (1: queue slot, 2: wavefront pixel offset, 3: pushed pixel offset), and the
+// access is skipped instead of made. Read back with recon_checks().
+#ifdef RECON_CHECKS
+__device__ unsigned g_check_violations;
+__device__ unsigned g_check_first;
+__device__ __noinline__ bool check_fail(unsigned where)
+{
+    atomicAdd(&g_check_violations, 1u);
+    atomicCAS(&g_check_first, 0u, where);
+    return false;
+}
+#define RK_CHECK(cond, where) ((cond) ? true : check_fail(where))
+#else
+#define RK_CHECK(cond, where) true
+#endif
+
 __device__ __forceinline__ unsigned long long gtimer()
 {
     unsigned long long t;
@@ -536,6 +555,9 @@ __device__ __forceinline__ unsigned lanemask_lt()
 template <int BH>
 __device__ __forceinline__ void put_entry(Smem<BH> &S, uint16_t *gsp, int lvl, unsigned slot, uint16_t v)
 {
+    if (!RK_CHECK(v >= (unsigned)(PW * 4) && v < (unsigned)((BH + 1) * PW * 4) &&
+                  (unsigned)(v % (PW * 4) - XOFF) < (unsigned)BW, 3))
+        return;
     if (slot < (unsigned)QCAP) S.q[lvl][slot] = v;
     else if (slot - QCAP < (unsigned)GCAP) gsp[lvl * GCAP + (slot - QCAP)] = v;
     else S.overflow = 1;
@@ -544,6 +566,7 @@ __device__ __forceinline__ void put_entry(Smem<BH> &S, uint16_t *gsp, int lvl, u
 template <int BH>
 __device__ __forceinline__ uint16_t get_entry(const Smem<BH> &S, const uint16_t *gsp, int lvl, unsigned i)
 {
+    if (!RK_CHECK(i < (unsigned)(QCAP + GCAP), 1)) return (uint16_t)(PW * 4 + XOFF);
     return i < (unsigned)QCAP ? S.q[lvl][i] : gsp[lvl * GCAP + (i - QCAP)];
 }
 
@@ -720,13 +743,21 @@ struct RowBits {
 // any result is awaited; only the rare attempt that lost a race on its word
 // retries. A neighbour counts as raised only if this thread's update stuck,
 // so each raise is pushed once. Returns the mask of raised neighbours.
-template <int CONN>
+template <int BH, int CONN>
 __device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t *Jb, const uint8_t *Ib,
                                            unsigned p, uint32_t v, bool act, RowBits &rows)
 {
     constexpr int RB = PW * 4;
     const int off8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
     const int off4[4] = {-RB, -1, 1, RB};
+#ifdef RECON_CHECKS
+    // an interior pixel of the block: rows 1 .. BH of J, columns XOFF .. XOFF + BW - 1
+    if (act && !RK_CHECK(p >= (unsigned)RB && p < (unsigned)((BH + 1) * RB) && (unsigned)(p % RB - XOFF) < (unsigned)BW,
+                         2)) {
+        act = false;
+        p = RB + XOFF;
+    }
+#endif
     // The neighbour's whole word is read once: its byte decides the
     // propagation condition and the word is the expected value of the
     // compare-and-swap (one dependent shared-memory round trip fewer).
@@ -818,7 +849,7 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
                 const unsigned p = act ? (unsigned)ring[(head + lane) & (RING - 1)] : safe_p;
                 const uint32_t v = act ? Jb[p] : 0u;
                 __syncwarp();
-                const unsigned raised = expand<CONN>(S.J, Jb, Ib, p, v, act, rows);
+                const unsigned raised = expand<BH, CONN>(S.J, Jb, Ib, p, v, act, rows);
                 // slots by direction: one ballot per neighbour direction, no prefix-sum chain
                 unsigned bal[CONN], tot = 0;
 #pragma unroll
@@ -860,7 +891,7 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
             const bool act = i < navail;
             const unsigned p = act ? get_entry(S, gsp, src, i) : safe_p;
             const uint32_t v = act ? Jb[p] : 0u;
-            const unsigned raised = expand<CONN>(S.J, Jb, Ib, p, v, act, rows);
+            const unsigned raised = expand<BH, CONN>(S.J, Jb, Ib, p, v, act, rows);
             unsigned bal[CONN], tot = 0;
 #pragma unroll
             for (int k = 0; k < CONN; ++k) {
@@ -1305,6 +1336,31 @@ extern "C" cudaError_t rk_launch_init(int grid, const rk::Params *P, cudaStream_
 {
     rk::recon_init_kernel<<<grid, 256, 0, st>>>(*P);
     return cudaGetLastError();
+}
+
+// Bounds-checked build only: *enabled = 1, the number of failed checks since
+// the last reset and the where-code of the first. Other builds: *enabled = 0.
+extern "C" int recon_checks(int *enabled, unsigned *violations, unsigned *first, int reset)
+{
+    if (!enabled || !violations || !first) return 1;
+#ifdef RECON_CHECKS
+    *enabled = 1;
+    if (cudaMemcpyFromSymbol(violations, rk::g_check_violations, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemcpyFromSymbol(first, rk::g_check_first, sizeof(unsigned)) != cudaSuccess)
+        return 4;
+    if (reset) {
+        const unsigned z = 0;
+        if (cudaMemcpyToSymbol(rk::g_check_violations, &z, sizeof(z)) != cudaSuccess ||
+            cudaMemcpyToSymbol(rk::g_check_first, &z, sizeof(z)) != cudaSuccess)
+            return 4;
+    }
+#else
+    *enabled = 0;
+    *violations = 0;
+    *first = 0;
+    (void)reset;
+#endif
+    return 0;
 }
 
 extern "C" cudaError_t rk_launch_fill(const rk::TileDesc *tiles, const int *list, int nlist, cudaStream_t st)
