@@ -250,7 +250,9 @@ int recon_autotune_cache_load(recon_ctx *ctx, const int *entries, int count);
 
 /* Features of n tiles into feat (n x 20 fp32): [0..15] fraction of pixels with
  * (I - J) >> 4 == k, [16] fraction with I >= 100 (blob pixels), [17] fraction
- * with J == 0, [18] log2(H) / 12, [19] log2(W) / 12. One pass over I and J. Syncs. */
+ * with J == 0, [18] log2(H) / 12, [19] log2(W) / 12. One pass over I and J.
+ * Erosion and FillHoles tiles are described by their complemented values (for
+ * FillHoles with J = 0 inside), the dilation problem the kernel solves. Syncs. */
 int recon_features(recon_ctx *ctx, const recon_tile *tiles, int n, float *feat);
 
 /* Y (n x 2) = MLP(theta, X (n x 20)). */
