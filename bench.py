@@ -12,7 +12,13 @@ fill-holes markers) as one 4-tile batch. Metric: reconstructed Mpix/s.
 dilation), "erode" (reconstruction by erosion of the complemented pairs, the
 same propagation work as the dilation tiles) or "fill_holes" (FillHoles of
 every distinct (mask, connectivity) of the workload; the output needs no
-reset, so a step is the library call alone).
+reset, so a step is the library call alone) or "dt" (the distance transform of
+the workload's masks: objects I >= 100 and the space between them).
+--compare adds the plain schedule, the per-tile launch loop, the learned
+schedule with and without its planning pass, and the sweep-only and
+queue-first halves of the method with their own rooflines. --microbench runs
+the random-access and atomic micro-benchmarks instead. --impl reference times
+the CPU oracle on the same workload (the reference arm).
 
 Timing: CUDA events on the library's stream around each step; L2 is flushed
 (a 512 MiB write) before every timed step, outside the events. Under torchrun
