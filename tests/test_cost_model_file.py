@@ -51,3 +51,14 @@ def test_checkpoint_rejects_bad_and_truncated(tmp_path):
     q.write_bytes(q.read_bytes()[:-100])
     with pytest.raises(ValueError):
         cost_model.load_checkpoint(str(q))
+
+
+def test_tuning_cache_file_roundtrip(tmp_path):
+    from paper_1311_0378_gb300 import tuning
+    entries = [(18, 2, 0, 128, 4, 1, 512), (24, 3, 1, 64, 2, 0, 0)]
+    p = str(tmp_path / "tune.json")
+    tuning.write_entries(p, entries)
+    assert tuning.read_entries(p) == entries
+    (tmp_path / "bad.json").write_text('{"entries": [{"size_bucket": 1}]}')
+    with pytest.raises(ValueError):
+        tuning.read_entries(str(tmp_path / "bad.json"))
