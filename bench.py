@@ -2,11 +2,14 @@
 """Throughput of grayscale morphological reconstruction on GB300.
 
 One step = the whole reconstruction of one batch of synthetic tiles through
-the C ABI (marker reset from its pristine copy, validation, scan pairs, queue
-propagation, neighbour notification, persistent launch replayed from a CUDA
-graph). Default workload "single4096": one 4096 x 4096 mask with 6711 blobs,
-reconstructed four times per step (4- and 8-connectivity x h-dome and
-fill-holes markers) as one 4-tile batch. Metric: reconstructed Mpix/s.
+the C ABI (marker reset from its pristine copy, the learned schedule's
+planning pass, validation, scan pairs, queue propagation, neighbour
+notification, persistent launch replayed from a CUDA graph). Default workload
+"uneven1000": 1000 tiles whose heights and widths are drawn from
+{256, 512, ..., 4096} (4.7 Gpx, h-dome and fill-holes markers 50/50,
+8-connectivity), reconstructed in one persistent launch. Metric:
+reconstructed Mpix/s. "single4096" is one 4096 x 4096 mask reconstructed four
+times (4-/8-connectivity x both markers); "batch64" is 64 tiles of 4096 x 4096.
 
 --op selects the operation: "dilate" (the default, reconstruction by
 dilation), "erode" (reconstruction by erosion of the complemented pairs, the
@@ -14,16 +17,21 @@ same propagation work as the dilation tiles) or "fill_holes" (FillHoles of
 every distinct (mask, connectivity) of the workload; the output needs no
 reset, so a step is the library call alone) or "dt" (the distance transform of
 the workload's masks: objects I >= 100 and the space between them).
---compare adds the plain schedule, the per-tile launch loop, the learned
-schedule with and without its planning pass, and the sweep-only and
-queue-first halves of the method with their own rooflines. --microbench runs
-the random-access and atomic micro-benchmarks instead. --impl reference times
-the CPU oracle on the same workload (the reference arm).
+The line's "compare" block (skip it with --no-compare) times the plain
+schedule, the per-tile launch loop, the learned schedule with and without its
+planning pass, and the sweep-only and queue-first halves of the method with
+their own rooflines. "cpu_baseline" is the CPU oracle on a bounded sample of
+the workload, on all host cores and on one core. --microbench runs the
+random-access and atomic micro-benchmarks instead; --tile T reconstructs one
+tile alone (a small fixed case for profilers); --subset n keeps every n-th
+tile; --impl reference times the CPU oracle on the same workload (the
+reference arm).
 
 Timing: CUDA events on the library's stream around each step; L2 is flushed
 (a 512 MiB write) before every timed step, outside the events. Under torchrun
-each rank runs the same batch (tiles are independent: weak scaling) and the
-slowest rank's time counts.
+the job is the workload's family with N times its tiles, split across the N
+ranks by longest-processing-time-first (weak scaling, no collective on the
+data path), and the slowest rank's time counts.
 """
 from __future__ import annotations
 
@@ -156,9 +164,9 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows), "interval_ms": self.INTERVAL_MS}
 
 
-def workload_tiles(name, op="dilate"):
+def workload_tiles(name, op="dilate", copies=1):
     import synth
-    w = synth.workload(name)
+    w = synth.scaled_workload(name, copies)
     tiles = w.tiles
     if op == "fill_holes" and name == "single4096":
         # one shared mask: the marker kinds collapse, one tile per connectivity
@@ -168,6 +176,21 @@ def workload_tiles(name, op="dilate"):
                 seen.add(t.conn)
                 tiles.append(t)
     return w, tiles, name == "single4096"
+
+
+def job_tiles(name, op, world, rank, subset=1):
+    """The whole job's tiles and this rank's share. With N ranks the job is
+    the workload's family with N times its tiles (weak scaling: the same work
+    per GPU), split across ranks by longest-processing-time-first on the pixel
+    count; tiles are independent, so no data crosses ranks. subset > 1 keeps
+    every subset-th tile of the job (a stated smaller case, e.g. for a
+    profiler capture)."""
+    from paper_1311_0378_gb300.shard import lpt_shards
+    w, tiles, shared = workload_tiles(name, op, world)
+    tiles = list(tiles)[::max(1, subset)]
+    shards = lpt_shards([t.H * t.W for t in tiles], world)
+    mine = [tiles[i] for i in sorted(shards[rank])]
+    return w, tiles, mine, shared
 
 
 def complement_(t):
@@ -211,18 +234,43 @@ def oracle_op(pairs, conns, op, nthreads):
     return used
 
 
-def cpu_baseline(w, tiles, shared_mask, budget_tiles=None, op="dilate"):
-    """The CPU oracle (sweeps to stability), as it stands, on host threads."""
+def baseline_samples(name, tiles):
+    """Bounded samples of the workload for the CPU oracle: (all-cores sample,
+    one-core sample), each a list of tile indices."""
+    n = len(tiles)
+    if n <= 8:
+        return list(range(n)), list(range(min(2, n)))
+    ncores = os.cpu_count() or 1
+    stride = max(1, n // max(ncores, 16))
+    many = list(range(0, n, stride))[:max(ncores, 16)]
+    one = many[::max(1, len(many) // 4)][:4] if n > 64 else many[:1]
+    return many, one
+
+
+def cpu_baseline(w, tiles, shared_mask, op="dilate"):
+    """The CPU oracle (sweeps to stability), as it stands, on a bounded sample
+    of the workload: once with one tile per host thread on all cores, once on
+    a single core. Returns the JSON object of the bench line."""
     import synth
-    sample = tiles if budget_tiles is None else tiles[:budget_tiles]
-    pairs = synth.generate(sample, w.seed)
-    if op == "erode":   # input preparation, outside the timing
-        pairs = [(255 - I, 255 - J) for I, J in pairs]
-    t0 = time.perf_counter()
-    used = oracle_op(pairs, [t.conn for t in sample], op, len(sample))
-    dt = time.perf_counter() - t0
-    px = sum(t.H * t.W for t in sample)
-    return px, dt, used, "%d of %d tiles (%s), full size, op %s" % (len(sample), len(tiles), w.name, op)
+    many, one = baseline_samples(w.name, tiles)
+    out = {}
+    for key, idx, threads in (("all_cores", many, os.cpu_count() or 1), ("one_core", one, 1)):
+        sample = [tiles[i] for i in idx]
+        pairs = synth.generate(sample, w.seed)
+        if op == "erode":   # input preparation, outside the timing
+            pairs = [(255 - I, 255 - J) for I, J in pairs]
+        t0 = time.perf_counter()
+        used = oracle_op(pairs, [t.conn for t in sample], op, min(threads, len(sample)))
+        dt = time.perf_counter() - t0
+        px = sum(t.H * t.W for t in sample)
+        out[key] = {"value": round(px / dt / 1e6, 3), "cores": used, "seconds": round(dt, 2),
+                    "sample": "tiles %s of %d (%s), full size, op %s" % (
+                        idx if len(idx) <= 8 else "%d..%d step %d (%d tiles)" % (idx[0], idx[-1], idx[1] - idx[0],
+                                                                              len(idx)),
+                        len(tiles), w.name, op)}
+    return {"value": out["all_cores"]["value"], "unit": "Mpix/s", "cores": out["all_cores"]["cores"],
+            "kind": "oracle", "sample": out["all_cores"]["sample"], "seconds": out["all_cores"]["seconds"],
+            "host_cores": os.cpu_count(), "one_core": out["one_core"]}
 
 
 def run_reference(args):
@@ -534,14 +582,52 @@ def phase_rooflines(rc, ctx, stream, Js, J0, desc, tiles, px, flush):
     return out
 
 
+def run_tile_mode(args):
+    """--tile T: reconstructs tile T of the workload alone through recon_run_op,
+    --steps times after --warmup runs, and prints one JSON line per run with
+    its device time and work counters (a small, fixed case for profilers)."""
+    import torch
+    import paper_1311_0378_gb300 as rc
+    from paper_1311_0378_gb300 import build as rbuild
+    import synth
+    rbuild.build()
+    w = synth.workload(args.workload)
+    spec = w.tiles[args.tile]
+    I, J = synth.tile_pair(spec, w.seed)
+    if args.op == "erode":
+        I, J = 255 - I, 255 - J
+    ctx = rc.recon_init(0, 0, 0)
+    for kv in args.param:
+        k, v = kv.split("=")
+        rc.check(rc.recon_set_param(ctx, getattr(rc, "RECON_P_" + k.upper()), int(v)), kv)
+    dI = torch.from_numpy(I).cuda()
+    J0 = torch.from_numpy(J).cuda()
+    dJ = J0.clone()
+    torch.cuda.synchronize()
+    for r in range(args.warmup + args.steps):
+        dJ.copy_(J0)
+        torch.cuda.synchronize()
+        rc.check(rc.recon_run_op(ctx, dI.data_ptr(), dJ.data_ptr(), spec.H, spec.W, spec.conn, OP_CODE[args.op]),
+                 "recon_run_op")
+        rc.check(rc.recon_sync_for(ctx, 120000), "sync")
+        if r >= args.warmup:
+            print(json.dumps({"tile": args.tile, "workload": w.name, "H": spec.H, "W": spec.W, "conn": spec.conn,
+                              "marker": spec.marker, "op": args.op, "run": r - args.warmup,
+                              "kernel_ms": round(rc.recon_last_kernel_ms(ctx), 4),
+                              **rc.recon_get_work(ctx, 1)[0]}), flush=True)
+    rc.recon_free(ctx)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="single4096",
-                    choices=["single4096", "single512", "batch64", "uneven1000"])
+    ap.add_argument("--workload", default="uneven1000",
+                    choices=["uneven1000", "batch64", "single4096", "single512"],
+                    help="uneven1000 (default): 1000 tiles of uneven sizes, 4.7 Gpx, one persistent launch")
     ap.add_argument("--op", default="dilate", choices=OPS,
                     help="dilate: reconstruction by dilation; erode: by erosion (complemented pairs); "
                          "fill_holes: FillHoles of the masks")
@@ -550,8 +636,14 @@ def main():
     ap.add_argument("--block-h", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=-99)
     ap.add_argument("--bands", type=int, default=0)
-    ap.add_argument("--compare", action="store_true",
-                    help="also time the per-tile launch loop and the learned schedule")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the plain schedule, per-tile launch loop and the two halves of the method")
+    ap.add_argument("--subset", type=int, default=1,
+                    help="keep every n-th tile of the job (a stated smaller case, e.g. for ncu captures)")
+    ap.add_argument("--tile", type=int, default=-1,
+                    help="reconstruct this one tile of the workload alone and print its time and work")
+    ap.add_argument("--param", action="append", default=[],
+                    help="with --tile: KEY=VALUE context parameter, KEY a RECON_P_* suffix")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--schedule", default="learned", choices=["learned", "plain"],
                     help="learned: the cost model picks each tile's variant and the packing order "
@@ -563,6 +655,8 @@ def main():
         return run_reference(args)
     if args.microbench:
         return run_microbench(args)
+    if args.tile >= 0:
+        return run_tile_mode(args)
     if args.op == "dt":
         return run_dt(args)
 
@@ -584,7 +678,7 @@ def main():
     if dist:
         dist.barrier()
 
-    w, tiles, shared = workload_tiles(args.workload, args.op)
+    w, job, tiles, shared = job_tiles(args.workload, args.op, world, rank, args.subset)
     Is_h, Js_h = gen_host(w, tiles, shared, args.op)
     opc = OP_CODE[args.op]
     reset_j = args.op != "fill_holes"   # a FillHoles output needs no reset
@@ -622,7 +716,8 @@ def main():
               "schedule": args.schedule,
               "cost_model": ({"tiles": model_meta.get("tiles"), "variants": model_meta.get("variants")}
                              if model_meta else None)}
-    px = sum(t.H * t.W for t in tiles)
+    px = sum(t.H * t.W for t in tiles)          # this rank's pixels per step
+    job_px = sum(t.H * t.W for t in job)        # every rank's pixels per step
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def step():
@@ -659,11 +754,16 @@ def main():
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * px / (ms / 1e3) / 1e6
+    value = job_px / (ms / 1e3) / 1e6
 
     compare = None
-    if args.compare and len(tiles) > 1:
+    if not args.no_compare and len(tiles) > 1:
         compare = compare_schedules(rc, ctx, stream, Is, Js, J0, tiles, desc, px, flush, args)
+        compare["learned_with_planning_vs_plain"] = (
+            round(compare["batched_learned_with_planning_mpix_s"] / compare["batched_plain_mpix_s"], 3)
+            if compare.get("batched_learned_with_planning_mpix_s") else None)
+        compare["batched_plain_vs_per_tile_loop"] = round(
+            compare["batched_plain_mpix_s"] / compare["per_tile_loop_mpix_s"], 3)
         if args.op == "dilate":
             compare["phases"] = phase_rooflines(rc, ctx, stream, Js, J0, desc, tiles, px, flush)
 
@@ -676,11 +776,18 @@ def main():
             a.copy_(b)
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         rc.check(rc.recon_batch_host(ctx, htiles), "recon_batch_host")
         if i > 0:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e = world * px / (statistics.median(e2e_ms) / 1e3) / 1e6
+    e2e_t = statistics.median(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e = job_px / (e2e_t / 1e3) / 1e6
     h2d = sum((2 if reset_j else 1) * t.H * t.W for t in tiles)
     d2h = px
     rc.recon_free(ctx)
@@ -694,20 +801,28 @@ def main():
     alg = ALG_BYTES_PER_PX[args.op]
     achieved = alg * px / (kms / 1e3) / 1e9
     traffic_key = w.name if args.op == "dilate" else "%s:%s" % (w.name, args.op)
+    traffic = measured_traffic(traffic_key) if args.subset == 1 and world == 1 else None
+    roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / pk["hbm_gbs"], 5), "traffic": traffic,
+            "kernel": "recon_persistent", "kernel_ms": round(kms, 4),
+            "alg_bytes_per_px": alg, "alg_bytes_per_launch": alg * px, "peak_source": src,
+            "limiter": "propagation depth and shared-memory latency of thin wavefronts (not DRAM)"}
+    if traffic:
+        roof["dram_GBps"] = round(traffic / (kms / 1e3) / 1e9, 2)
+        roof["dram_frac"] = round(traffic / (kms / 1e3) / 1e9 / pk["hbm_gbs"], 5)
     line = {
         "metric": "reconstructed Mpix/s", "value": round(value, 2), "unit": "Mpix/s",
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": w.name, "op": args.op, "tiles": len(tiles), "pixels_per_step": px,
+        "config": {"workload": w.name, "op": args.op, "tiles": len(job), "pixels_per_step": job_px,
+                   "tiles_per_rank": len(tiles), "subset": args.subset,
+                   "sharding": "LPT on pixel count, no collective on the data path" if world > 1 else None,
                    "conn": sorted({t.conn for t in tiles}),
                    "markers": "h-dome + fill-holes" if reset_j else "border (FillHoles)",
                    "l2": "flushed before each timed step (512 MiB write)", "bit_exact": "see tests -m gpu",
                    **params},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": round(achieved / pk["hbm_gbs"], 5), "traffic": measured_traffic(traffic_key),
-                     "kernel": "recon_persistent", "kernel_ms": round(kms, 4),
-                     "alg_bytes_per_px": alg, "peak_source": src},
+        "roofline": roof,
         "e2e": {"value": round(e2e, 2), "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         # per step: init + persistent kernel, plus features, finalize and MLP forward
         # when learned, plus the marker kernel for FillHoles
@@ -715,10 +830,8 @@ def main():
         "compare": compare,
         "clocks": clk.summary(),
     }
-    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
-        cpx, cdt, used, sample = cpu_baseline(w, tiles, shared, None if len(tiles) <= 8 else 4, args.op)
-        line["cpu_baseline"] = {"value": round(cpx / cdt / 1e6, 3), "unit": "Mpix/s", "cores": used,
-                                "kind": "oracle", "sample": sample, "seconds": round(cdt, 2)}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, tiles, shared, args.op)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

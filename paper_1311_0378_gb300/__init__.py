@@ -5,6 +5,9 @@ Argument marshalling only: every step of the reconstruction runs in the CUDA
 kernels behind the C ABI. Functions keep the C names; image arguments are
 device addresses (ints, e.g. ``tensor.data_ptr()`` of contiguous uint8 CUDA
 tensors), except in the ``*_host`` entry points, which take host addresses.
+``run(I, J, conn)`` and ``batch(pairs, conn)`` take the tensors themselves,
+check that they are contiguous 2-D uint8 CUDA tensors, and call the same
+entry points.
 There is no fallback: if librecon.so is missing or fails to load, every call
 raises.
 """
@@ -311,6 +314,79 @@ def recon_trace(ctx, n: int):
 def recon_run_noalloc(I: int, J: int, H: int, W: int, conn: int, stream: int = 0) -> int:
     """Allocation-free single-tile reconstruction (device pointers; waits)."""
     return lib().recon_run_noalloc(I, J, H, W, conn, ctypes.c_void_p(stream or None))
+
+
+# ---- tensor-level calls: argument checks, then the C calls above ----
+
+_contexts = {}
+
+
+def _check_pair(I, J):
+    """I and J must be contiguous 2-D uint8 CUDA tensors of one shape on one
+    device (the C ABI takes their device addresses, row stride = W)."""
+    import torch
+    for name, t in (("I", I), ("J", J)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("%s must be a torch.Tensor" % name)
+        if t.dtype != torch.uint8:
+            raise TypeError("%s must be uint8, got %s" % (name, t.dtype))
+        if t.device.type != "cuda":
+            raise ValueError("%s must be a CUDA tensor, got device %s" % (name, t.device))
+        if t.dim() != 2:
+            raise ValueError("%s must be 2-D (H, W), got shape %s" % (name, tuple(t.shape)))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if I.shape != J.shape or I.device != J.device:
+        raise ValueError("I %s on %s and J %s on %s differ in shape or device"
+                         % (tuple(I.shape), I.device, tuple(J.shape), J.device))
+
+
+def context_for(device, stream=None, flags: int = RECON_FLAG_SYNC):
+    """A context kept per (device index, stream, flags) for the tensor calls;
+    `stream` is a torch.cuda.Stream (None: torch's current stream on that
+    device). RECON_FLAG_SYNC makes each call raise on a device error."""
+    import torch
+    dev = torch.device(device)
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    st = stream if stream is not None else torch.cuda.current_stream(idx)
+    key = (idx, st.cuda_stream, flags)
+    if key not in _contexts:
+        _contexts[key] = recon_init(idx, st.cuda_stream, flags)
+    return _contexts[key]
+
+
+def run(I, J, conn: int = 8, op: int = RECON_OP_DILATE, ctx=None):
+    """Reconstructs J in place under I (Table II; Algorithm 1 with the hybrid
+    scan + queue schedule of Sec. V-C) and returns J. I, J: contiguous uint8
+    CUDA tensors of shape (H, W); op: RECON_OP_DILATE (J <= I), RECON_OP_ERODE
+    (J >= I) or RECON_OP_FILL_HOLES (J receives FillHoles(I)). Runs on torch's
+    current stream unless `ctx` is given; raises ReconError on failure."""
+    _check_pair(I, J)
+    c = ctx if ctx is not None else context_for(J.device)
+    check(recon_run_op(c, I.data_ptr(), J.data_ptr(), int(I.shape[0]), int(I.shape[1]), conn, op), "run")
+    return J
+
+
+def batch(pairs, conn: int = 8, op: int = RECON_OP_DILATE, ctx=None):
+    """Reconstructs every (I, J) pair in one persistent launch, each J in place,
+    and returns the list of J. Tensors as for run(); tiles may differ in size
+    and must not share memory. Raises ReconError (with the failing tile from
+    recon_last_error_tile in the message) on failure."""
+    pairs = list(pairs)
+    if not pairs:
+        raise ValueError("batch needs at least one (I, J) pair")
+    for I, J in pairs:
+        _check_pair(I, J)
+    dev = pairs[0][1].device
+    if any(J.device != dev for _, J in pairs):
+        raise ValueError("all tiles of a batch must be on one device")
+    c = ctx if ctx is not None else context_for(dev)
+    tiles = [(I.data_ptr(), J.data_ptr(), int(I.shape[0]), int(I.shape[1]), int(I.shape[1]), conn, op)
+             for I, J in pairs]
+    st = recon_batch(c, tiles)
+    if st != RECON_OK:
+        raise ReconError(st, "batch (first failing tile %d)" % recon_last_error_tile(c))
+    return [J for _, J in pairs]
 
 
 # ---- device micro-benchmarks (current device, default stream; they wait) ----

@@ -102,6 +102,33 @@ def _uneven_tiles(seed: int, n: int, conn: int = 8) -> Tuple[TileSpec, ...]:
     return tuple(out)
 
 
+def _batch64_tiles(n: int) -> Tuple[TileSpec, ...]:
+    """4096 x 4096 tiles, blobs uniform in [0, H*W/1000], r 4..12, 8-conn,
+    marker h-dome or fill-holes with probability 1/2 each (seed 3)."""
+    tiles = []
+    for t in range(n):
+        nb = _u(3, t, 3) % (round(4096 * 4096 / 1000) + 1)
+        tiles.append(TileSpec(4096, 4096, nb, 4, 12, _u(3, t, 4) & 1, 8, t))
+    return tuple(tiles)
+
+
+def scaled_workload(name: str, copies: int) -> Workload:
+    """The workload's family with `copies` times as many tiles (weak scaling
+    across GPUs): batch64 and uneven1000 continue their tile sequences (tile
+    indices 0 .. copies * n - 1 of the same seed, so copies = 1 is the workload
+    itself); single512 and single4096 repeat their tiles."""
+    w = workload(name)
+    if copies == 1:
+        return w
+    if copies < 1:
+        raise ValueError("copies must be >= 1")
+    if name == "batch64":
+        return Workload(name, w.seed, _batch64_tiles(64 * copies))
+    if name == "uneven1000":
+        return Workload(name, w.seed, _uneven_tiles(w.seed, 1000 * copies))
+    return Workload(name, w.seed, w.tiles * copies)
+
+
 def workload(name: str) -> Workload:
     """The named synthetic workloads.
 
@@ -122,11 +149,7 @@ def workload(name: str) -> Workload:
         return Workload(name, 2, tuple(TileSpec(4096, 4096, nb, 4, 12, m, c, 0)
                                        for c in (4, 8) for m in (HDOME, FILLHOLES)))
     if name == "batch64":
-        tiles = []
-        for t in range(64):
-            nb = _u(3, t, 3) % (round(4096 * 4096 / 1000) + 1)
-            tiles.append(TileSpec(4096, 4096, nb, 4, 12, _u(3, t, 4) & 1, 8, t))
-        return Workload(name, 3, tuple(tiles))
+        return Workload(name, 3, _batch64_tiles(64))
     if name == "uneven1000":
         return Workload(name, 4, _uneven_tiles(4, 1000))
     if name == "train20k":
