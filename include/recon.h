@@ -82,7 +82,11 @@ typedef struct {
     int op;             /* RECON_OP_*; 0 (dilation) when zero-initialised */
 } recon_tile;
 
-/* Creates a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
+/* Creates a context on CUDA device `device`: the library's scratch for the
+ * state Algorithm 1 (Sec. II-B) keeps beside the image D it updates in place --
+ * the wavefront queues' overflow areas, per-block state and work list, tile
+ * descriptors and status words -- plus the cost model. It owns no image data.
+ * `cuda_stream` is a cudaStream_t
  * (NULL: the context creates its own non-blocking stream). flags: RECON_FLAG_*.
  * The environment variables RECON_BLOCK_H, RECON_SWEEPS, RECON_BANDS,
  * RECON_GRID, RECON_WAIT_NS, RECON_ORDER, RECON_TMA, RECON_REVISIT_SCANS and
@@ -132,10 +136,16 @@ int recon_sync(recon_ctx *ctx);
 /* Index of the first tile of the last batch that failed, or -1. Syncs. */
 int recon_last_error_tile(recon_ctx *ctx);
 
-/* Frees the context and its scratch memory (syncs first). NULL is accepted. */
+/* Frees the context and its scratch memory (the queue and work-list state of
+ * Algorithm 1, Sec. II-B; see recon_init) after waiting for its stream. The
+ * caller's images are not touched. NULL is accepted. */
 int recon_free(recon_ctx *ctx);
 
-/* Static description of a status code. */
+/* Static description of a status code: the argument checks, the precondition
+ * of the operation (Table II's reconstruction needs J <= I; its dual J >= I),
+ * allocation and runtime failures, and the bounded waits of the wavefront
+ * propagation (Algorithm 1's loop "while the queue is not empty" runs under
+ * iteration and time limits). The string is static; never NULL. */
 const char *recon_strerror(int status);
 
 /* Tunables (recon_set_param / recon_get_param). */
@@ -153,7 +163,7 @@ enum {
     RECON_P_TRACE = 9,       /* diagnostics: 1 = kernels record per-warp progress in mapped
                                 host memory (read with recon_trace, even while running) */
     RECON_P_LAST_ABORT = 10, /* read-only: which device-side bound ran out in the last call
-                                (0 = none; 1 rerun, 2 overflow, 3 levels, 4 scans, 5 CAS,
+                                (0 = none; 1 rerun, 2 overflow, 3 levels, 4 scans, 5 unused,
                                 6 notify, 7 ring slot, 8 idle wait, 9 ring push, 10 TMA) */
     RECON_P_REVISIT_SCANS = 11, /* scan pairs a block runs when revisited (after a neighbour
                                    raised its halo) before its queue phase; default 0 */
@@ -204,8 +214,10 @@ int recon_last_kernel_ms(recon_ctx *ctx, float *ms);
  * is allocated: the scratch space is one 11 MiB array compiled into the
  * library, which every GPU that loads the library holds until the process
  * exits. I, J: device pointers, row stride = W, J <- R in place; runs on
- * `cuda_stream` (NULL = the default stream) of the current device and waits
- * for it. The first call on each device looks up the array's device address;
+ * `cuda_stream` (NULL = the default stream) of the current device and blocks
+ * the calling host thread until that stream has finished the call (it waits on
+ * that stream only; the descriptor upload from host stack memory and the status
+ * read-back are ordered on it too). The first call on each device looks up the array's device address;
  * make that first call outside any stream capture. Limits: at most 4096 blocks
  * of 64 x 128 pixels (e.g. 4096 x 8192); larger inputs return RECON_EINVAL.
  * Every call reuses the same array (cleared where it must start at zero), so

@@ -338,7 +338,8 @@ static int stage_meta(recon_ctx *c, const recon_tile *tiles, int n, const int *v
 {
     const MetaLayout L = meta_layout(n);
     const size_t off_order = L.off_order, off_base = L.off_base, total = L.total;
-    // the previous call's copy out of the staging buffer must be done
+    // the previous call's copy out of the staging buffer must be done (its
+    // event is recorded right after that copy, not after the kernels)
     CK(cudaEventSynchronize(c->meta_free));
     if (c->cap_hmeta < total) {
         if (c->h_meta) cudaFreeHost(c->h_meta);
@@ -521,19 +522,22 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
     c->last_err_tile = -1;
     const bool use_graph = !(c->flags & RECON_FLAG_NO_GRAPH);
     if (use_graph && c->gexec && sig == c->gsig) {
+        // the graph records meta_free itself, right after its descriptor copy
         CK(cudaGraphLaunch(c->gexec, c->stream));
-        CK(cudaEventRecord(c->meta_free, c->stream));
     } else {
         drop_graph(c);
         cudaGraph_t g = nullptr;
         if (use_graph) CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        // inside a capture, only an external record becomes an event node
+        const unsigned evf = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
         cudaError_t e = cudaMemcpyAsync(c->d_meta, c->h_meta, bytes, cudaMemcpyHostToDevice, c->stream);
+        // the staging buffer is free once this copy is done: the next call may
+        // refill it while this call's kernels still run
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->meta_free, c->stream, evf);
         // FillHoles tiles: write their border markers first
         if (e == cudaSuccess && nfill)
             e = rk_launch_fill(P.tiles, (const int *)(c->d_meta + ML.off_fill), nfill, c->stream);
         if (e == cudaSuccess) e = rk_launch_init(std::min(grid, 4 * c->sms), &P, c->stream);
-        // inside a capture, only an external record becomes a timed event node
-        const unsigned evf = use_graph ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev0, c->stream, evf);
         if (e == cudaSuccess) e = rk_launch_main(c->bh, grid, &P, c->stream);
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev1, c->stream, evf);
@@ -546,7 +550,6 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
             if (e == cudaSuccess) c->gsig.swap(sig);
             else drop_graph(c);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(c->meta_free, c->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
     c->launched = 1;

@@ -77,7 +77,7 @@ struct Params {
 
 // where-codes recorded in Ctl::abort when a bound runs out
 enum {
-    AB_RERUN = 1, AB_OVERFLOW = 2, AB_LEVELS = 3, AB_SCANS = 4, AB_CAS = 5, AB_NOTIFY = 6,
+    AB_RERUN = 1, AB_OVERFLOW = 2, AB_LEVELS = 3, AB_SCANS = 4, /* 5: unused */ AB_NOTIFY = 6,
     AB_RING = 7, AB_IDLE = 8, AB_PUSH = 9, AB_TMA = 10
 };
 

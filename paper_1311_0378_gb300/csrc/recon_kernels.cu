@@ -73,9 +73,9 @@ struct Smem {
     uint8_t eT[BW], eB[BW], eL[BH], eR[BH];  // edge values when neighbours last saw them
     unsigned rowmask[BH / 32];    // rows changed since the block was loaded
     unsigned pairmask[BH / 32];   // rows changed by the latest scan pair
+    unsigned claim[2][BH * BW / 32];  // wavefront ownership bits, one per interior pixel, by level parity
     unsigned cq[3];               // level sizes, rotating by level (see run_queue)
     unsigned item, tile, flag, overflow, notify, visited;
-    unsigned rpops;               // entries the per-warp rings processed since the seeding
     unsigned phase;               // parity of the TMA barrier's next completion
     unsigned abrt;                // block-uniform copy of the abort word
     Work acc;                     // thread 0: counters of consecutive visits to tile acc_tile
@@ -247,6 +247,11 @@ __device__ void tma_load_block(Smem<BH> &S, const Params &P, const TileDesc &D, 
         const unsigned long long mI = (unsigned long long)tm, mJ = (unsigned long long)(tm + 128);
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(mI) : "memory");
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" :: "l"(mJ) : "memory");
+        // Neighbour blocks wrote J (halo rows) with generic stores and published
+        // them through the block-state atomics this thread acquired; the TMA
+        // reads through the async proxy, so order generic before async accesses
+        // of global memory as well as of this CTA's shared memory.
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         const unsigned bytes = 2u * (unsigned)((BH + 2) * BOXW);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
@@ -596,7 +601,7 @@ __device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp, const unsigned *filter
 #pragma unroll
     for (int i = 0; i < BH / 32; ++i) rm[i] = filter ? filter[i] : 0u;
     __syncthreads();
-    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; S.rpops = 0; }
+    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = lane + W0;
     for (int y = 1 + (threadIdx.x >> 5); y <= BH; y += NT / 32) {
@@ -647,8 +652,6 @@ __device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp, const unsigned *filter
     return S.cq[0];
 }
 
-// byte-wise atomic max on the shared J: returns true if it raised the byte
-__device__ __forceinline__ bool atomic_max_u8(uint32_t *Jw, unsigned off, uint32_t v);
 
 // Seeding of a block that was already at its fixed point for its previous
 // halo (a revisit): its interior is unchanged since, so only the pixels next to
@@ -659,7 +662,7 @@ __device__ unsigned seed_frame(Smem<BH> &S, uint16_t *gsp)
 {
     constexpr int RB = PW * 4;
     constexpr int NFR = 2 * BW + 2 * (BH - 2);
-    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; S.rpops = 0; }
+    if (threadIdx.x == 0) { S.cq[0] = 0; S.cq[1] = 0; S.cq[2] = 0; S.overflow = 0; }
     __syncthreads();
     const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
     const uint8_t *Ib = (const uint8_t *)S.I;
@@ -698,58 +701,53 @@ __device__ unsigned seed_frame(Smem<BH> &S, uint16_t *gsp)
 }
 
 
-__device__ __forceinline__ bool atomic_max_u8(uint32_t *Jw, unsigned off, uint32_t v)
+
+// Neighbour k of a pixel, as (row, column) steps: 8-connectivity NW, N, NE,
+// W, E, SW, S, SE; 4-connectivity N, W, E, S.
+template <int CONN>
+__device__ __forceinline__ constexpr int nb_dy(int k)
 {
-    uint32_t *wp = Jw + (off >> 2);
-    const unsigned sh = (off & 3) * 8;
-    uint32_t old = *(volatile uint32_t *)wp;
-    for (int it = 0; it < (1 << 20); ++it) {
-        if (((old >> sh) & 0xFFu) >= v) return false;
-        const uint32_t nw = (old & ~(0xFFu << sh)) | (v << sh);
-        const uint32_t prev = atomicCAS(wp, old, nw);
-        if (prev == old) return true;
-        old = prev;
-    }
-    return false;  // unreachable in practice: every failed CAS means another byte of the word moved
+    return CONN == 8 ? (k < 3 ? -1 : (k < 5 ? 0 : 1)) : (k == 0 ? -1 : (k == 3 ? 1 : 0));
+}
+template <int CONN>
+__device__ __forceinline__ constexpr int nb_dx(int k)
+{
+    return CONN == 8 ? (k == 0 || k == 3 || k == 5 ? -1 : (k == 2 || k == 4 || k == 7 ? 1 : 0))
+                     : (k == 1 ? -1 : (k == 2 ? 1 : 0));
+}
+// byte offset of neighbour k in the shared-memory J / I rows
+template <int CONN>
+__device__ __forceinline__ constexpr int nb_off(int k)
+{
+    return nb_dy<CONN>(k) * (PW * 4) + nb_dx<CONN>(k);
 }
 
-// Marks row r (0-based block row) in four per-thread register words.
-struct RowBits {
-    unsigned w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-    __device__ __forceinline__ void mark(unsigned r)
-    {
-        const unsigned bit = 1u << (r & 31);
-        switch (r >> 5) {
-        case 0: w0 |= bit; break;
-        case 1: w1 |= bit; break;
-        case 2: w2 |= bit; break;
-        default: w3 |= bit; break;
-        }
-    }
-    template <int BH>
-    __device__ __forceinline__ void flush(Smem<BH> &S)
-    {
-        if (w0) atomicOr(&S.rowmask[0], w0);
-        if (BH > 32 && w1) atomicOr(&S.rowmask[1 % (BH / 32)], w1);
-        if (BH > 64 && w2) atomicOr(&S.rowmask[2 % (BH / 32)], w2);
-        if (BH > 64 && w3) atomicOr(&S.rowmask[3 % (BH / 32)], w3);
-    }
-};
+__device__ __forceinline__ uint32_t max3u(uint32_t a, uint32_t b, uint32_t c) { return __vimax3_u32(a, b, c); }
 
-// One pop of Algorithm 1's propagation phase for pixel offset p with current
-// value v: the neighbours q with J(q) < min(v, I(q)) (the propagation
-// condition) take that value by a byte-wise atomic max under the mask. All
-// neighbour tests, then all first compare-and-swap attempts, are issued before
-// any result is awaited; only the rare attempt that lost a race on its word
-// retries. A neighbour counts as raised only if this thread's update stuck,
-// so each raise is pushed once. Returns the mask of raised neighbours.
+// One pop of Algorithm 1's propagation phase, for frontier pixel p (a
+// shared-memory byte offset; act = false for an idle thread). Its neighbours q
+// that satisfy the propagation condition J(q) < min(J(p), I(q)) are
+// candidates. A candidate is updated by the one thread that claims it in this
+// level's ownership bitmap `claim` (an atomic OR, never retried); the owner
+// sets J(q) <- min(I(q), max over N(q) of J) -- one geodesic dilation step at
+// q (Table II) -- with a plain byte store. With one writer per pixel and level
+// and J only ever raised, no atomics touch J. An offer whose claim fails is
+// not lost: the owner's maximum includes J(p), written before the barrier
+// that opened this level, and a neighbour raised during the level is itself in
+// the next frontier and offers its value again.
+// The maxima of all directions come from a 5 x 5 window of J around p held in
+// registers: the 3 x 3 centre is read for the propagation test, the outer
+// ring only when this thread owns a candidate. Returns the raised neighbours
+// (bit k) with their new values in nv[k].
 template <int BH, int CONN>
-__device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t *Jb, const uint8_t *Ib,
-                                           unsigned p, uint32_t v, bool act, RowBits &rows)
+__device__ __forceinline__ unsigned expand(Smem<BH> &S, const unsigned *claim_ro, unsigned *claim, unsigned p,
+                                           bool act, uint32_t (&nv)[CONN])
 {
     constexpr int RB = PW * 4;
-    const int off8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
-    const int off4[4] = {-RB, -1, 1, RB};
+    const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
+    volatile uint8_t *Jm = (volatile uint8_t *)S.J;
+    const uint8_t *Ib = (const uint8_t *)S.I;
+    (void)claim_ro;
 #ifdef RECON_CHECKS
     // an interior pixel of the block: rows 1 .. BH of J, columns XOFF .. XOFF + BW - 1
     if (act && !RK_CHECK(p >= (unsigned)RB && p < (unsigned)((BH + 1) * RB) && (unsigned)(p % RB - XOFF) < (unsigned)BW,
@@ -758,38 +756,84 @@ __device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t 
         p = RB + XOFF;
     }
 #endif
-    // The neighbour's whole word is read once: its byte decides the
-    // propagation condition and the word is the expected value of the
-    // compare-and-swap (one dependent shared-memory round trip fewer).
-    uint32_t cv[CONN], old[CONN], seen[CONN];
+    if (!act) return 0;
+    const uint32_t v = Jb[p];
+    uint32_t iq[CONN], jq[CONN];
     unsigned cand = 0;
 #pragma unroll
     for (int k = 0; k < CONN; ++k) {
-        const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
-        cv[k] = min(v, (uint32_t)Ib[q]);
-        old[k] = ((const volatile uint32_t *)Jw)[q >> 2];
-        if (act && ((old[k] >> ((q & 3) * 8)) & 0xFFu) < cv[k]) cand |= 1u << k;
+        iq[k] = Ib[p + nb_off<CONN>(k)];
+        jq[k] = Jb[p + nb_off<CONN>(k)];
+        cand |= (jq[k] < min(v, iq[k]) ? 1u : 0u) << k;
     }
+    if (!cand) return 0;
+    // claims: every candidate is interior (a halo pixel's mask is 0 in S.I)
+    const int r = (int)(p / (unsigned)RB), x = (int)p - r * RB - XOFF;   // row 1..BH, column 0..BW-1
+    const int pb = (r - 1) * BW + x;
+    unsigned old[CONN];
 #pragma unroll
     for (int k = 0; k < CONN; ++k) {
-        seen[k] = old[k];
-        if ((cand >> k) & 1u) {
-            const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
-            const unsigned sh = (q & 3) * 8;
-            seen[k] = atomicCAS(Jw + (q >> 2), old[k], (old[k] & ~(0xFFu << sh)) | (cv[k] << sh));
+        const int qb = pb + nb_dy<CONN>(k) * BW + nb_dx<CONN>(k);
+        old[k] = ((cand >> k) & 1u) ? atomicOr(&claim[qb >> 5], 1u << (qb & 31)) : ~0u;
+    }
+    unsigned own = 0;
+#pragma unroll
+    for (int k = 0; k < CONN; ++k) {
+        const int qb = pb + nb_dy<CONN>(k) * BW + nb_dx<CONN>(k);
+        own |= ((old[k] >> (qb & 31)) & 1u) ? 0u : (1u << k);
+    }
+    if (!own) return 0;
+    // outer ring of the 5 x 5 window; rows p - 2 and p + 2 exist only for
+    // rows 2 .. BH - 1 (elsewhere they are needed only for halo pixels, which
+    // are never owned, so a valid row is read in their place)
+    const unsigned um = r >= 2 ? p - 2 * RB : p - RB, dm = r <= BH - 1 ? p + 2 * RB : p + RB;
+    uint32_t M[CONN];
+    if (CONN == 8) {
+        // w[a][b] = J(p + (a - 2) rows + (b - 2) columns)
+        uint32_t w[5][5];
+        w[0][0] = Jb[um - 2]; w[0][1] = Jb[um - 1]; w[0][2] = Jb[um]; w[0][3] = Jb[um + 1]; w[0][4] = Jb[um + 2];
+        w[4][0] = Jb[dm - 2]; w[4][1] = Jb[dm - 1]; w[4][2] = Jb[dm]; w[4][3] = Jb[dm + 1]; w[4][4] = Jb[dm + 2];
+        w[1][0] = Jb[p - RB - 2]; w[2][0] = Jb[p - 2]; w[3][0] = Jb[p + RB - 2];
+        w[1][4] = Jb[p - RB + 2]; w[2][4] = Jb[p + 2]; w[3][4] = Jb[p + RB + 2];
+        w[1][1] = jq[0]; w[1][2] = jq[1]; w[1][3] = jq[2];
+        w[2][1] = jq[3]; w[2][2] = v;     w[2][3] = jq[4];
+        w[3][1] = jq[5]; w[3][2] = jq[6]; w[3][3] = jq[7];
+        uint32_t h[5][3];   // h[a][c] = max over columns c .. c + 2 of row a
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) h[a][c] = max3u(w[a][c], w[a][c + 1], w[a][c + 2]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int a = nb_dy<8>(k) + 1, c = nb_dx<8>(k) + 1;   // top-left of q's 3 x 3 in the window
+            M[k] = max3u(h[a][c], h[a + 1][c], h[a + 2][c]);
         }
+    } else {
+        const uint32_t nw = Jb[p - RB - 1], ne = Jb[p - RB + 1], sw = Jb[p + RB - 1], se = Jb[p + RB + 1];
+        const uint32_t n2 = Jb[um], s2 = Jb[dm], w2 = Jb[p - 2], e2 = Jb[p + 2];
+        M[0] = max(max3u(n2, nw, ne), v);   // N(q) of q = N: its N, W, E and p
+        M[1] = max(max3u(w2, nw, sw), v);   // q = W
+        M[2] = max(max3u(e2, ne, se), v);   // q = E
+        M[3] = max(max3u(s2, sw, se), v);   // q = S
     }
     unsigned raised = 0;
 #pragma unroll
-    for (int k = 0; k < CONN; ++k)
-        if ((cand >> k) & 1u) {
-            const unsigned q = p + (CONN == 8 ? off8[k] : off4[k]);
-            const bool ok = (seen[k] == old[k]) || atomic_max_u8(Jw, q, cv[k]);
-            if (ok) {
-                raised |= 1u << k;
-                rows.mark(q / RB - 1);
-            }
+    for (int k = 0; k < CONN; ++k) {
+        nv[k] = min(iq[k], M[k]);
+        // jq[k] is current: q has one writer per level, and it is this thread
+        if (((own >> k) & 1u) && nv[k] > jq[k]) {
+            Jm[p + nb_off<CONN>(k)] = (uint8_t)nv[k];
+            raised |= 1u << k;
         }
+    }
+    if (raised) {   // rows changed since the block was loaded (0-based rows r - 2, r - 1, r)
+        const unsigned up = CONN == 8 ? (raised & 0x07u) : (raised & 0x1u);
+        const unsigned mid = CONN == 8 ? (raised & 0x18u) : (raised & 0x6u);
+        const unsigned dn = CONN == 8 ? (raised & 0xE0u) : (raised & 0x8u);
+        if (up) atomicOr(&S.rowmask[(r - 2) >> 5], 1u << ((r - 2) & 31));
+        if (mid) atomicOr(&S.rowmask[(r - 1) >> 5], 1u << ((r - 1) & 31));
+        if (dn) atomicOr(&S.rowmask[r >> 5], 1u << (r & 31));
+    }
     return raised;
 }
 
@@ -797,125 +841,52 @@ __device__ __forceinline__ unsigned expand(uint32_t *Jw, const volatile uint8_t 
 // Processes the wavefront level by level until it is empty (Algorithm 1's
 // propagation phase). Level L reads queue L % 2 and appends to (L + 1) % 2;
 // its size is counted in cq[(L + 1) % 3], and cq[(L + 2) % 3] is reset during
-// level L, so one barrier per level suffices. n0 = size of level 0 (counted in
-// cq[0]; the seeding pass zeroed cq[1], cq[2]). Returns entries processed.
+// level L, so one barrier per level suffices. Level L claims pixels in bitmap
+// claim[L % 2]; the other bitmap, last used by level L - 1, is cleared during
+// level L for level L + 1. n0 = size of level 0 (counted in cq[0]; the seeding
+// pass zeroed cq[1], cq[2]). Returns entries processed.
 template <int BH, int CONN>
 __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *gsp, unsigned n0,
                                         unsigned long long &nlevels)
 {
-    constexpr long MAX_LEVELS = 1l << 21;
-    constexpr int RING = QCAP / (NT / 32);   // entries of one warp's private ring
-    constexpr int ASYNC_MAX = RING / 2;      // levels at most this large go to the rings
-    static_assert((RING & (RING - 1)) == 0, "ring size must be a power of two");
-    constexpr int RB = PW * 4;
-    const int off8[8] = {-RB - 1, -RB, -RB + 1, -1, 1, RB - 1, RB, RB + 1};
-    const int off4[4] = {-RB, -1, 1, RB};
-    const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
-    const uint8_t *Ib = (const uint8_t *)S.I;
-    const int lane = threadIdx.x & 31;
-    const unsigned safe_p = RB + XOFF;   // an interior pixel for idle lanes
-    RowBits rows;
+    constexpr unsigned MAX_LEVELS = 1u << 21;
+    constexpr int NCW = BH * BW / 32;   // claim words per bitmap
     unsigned long long pops = 0;
+    for (int i = threadIdx.x; i < 2 * NCW; i += NT) (&S.claim[0][0])[i] = 0u;
+    __syncthreads();
     unsigned n = n0;
-    long L = 0;
-    while (n > 0) {
+    int src = 0, ccur = 0;   // queue buffer and level-size counter of the current level
+    for (unsigned L = 0; n > 0; ++L) {
         if (L > MAX_LEVELS) {
             if (threadIdx.x == 0) set_abort(P, AB_LEVELS);
-            break;
-        }
-        if (n <= (unsigned)ASYNC_MAX) {
-            // Thin fronts: every warp takes a quarter of this level into a
-            // private ring (in the other queue buffer) and drains it on its
-            // own, in FIFO batches of up to 32 entries, with warp-level
-            // synchronisation only. Children go to the same warp's ring; a ring
-            // that would overflow drops entries and raises S.overflow (the
-            // caller then re-seeds the block).
-            const int src = (int)(L & 1);
-            const int warp = threadIdx.x >> 5;
-            uint16_t *ring = &S.q[src ^ 1][warp * RING];
-            const unsigned lo = (unsigned)warp * n / (NT / 32), hi = (unsigned)(warp + 1) * n / (NT / 32);
-            for (unsigned i = lo + lane; i < hi; i += 32) ring[i - lo] = S.q[src][i];
-            __syncwarp();
-            unsigned head = 0, tail = hi - lo;
-            long batches = 0;
-            unsigned wpops = 0;   // this warp's ring entries
-            while (head < tail) {
-                if (++batches > MAX_LEVELS) {
-                    if (lane == 0) set_abort(P, AB_LEVELS);
-                    break;
-                }
-                const unsigned m = min(tail - head, 32u);
-                const bool act = (unsigned)lane < m;
-                const unsigned p = act ? (unsigned)ring[(head + lane) & (RING - 1)] : safe_p;
-                const uint32_t v = act ? Jb[p] : 0u;
-                __syncwarp();
-                const unsigned raised = expand<BH, CONN>(S.J, Jb, Ib, p, v, act, rows);
-                // slots by direction: one ballot per neighbour direction, no prefix-sum chain
-                unsigned bal[CONN], tot = 0;
-#pragma unroll
-                for (int k = 0; k < CONN; ++k) {
-                    bal[k] = __ballot_sync(FULL, (raised >> k) & 1u);
-                    tot += __popc(bal[k]);
-                }
-                if (tail + tot - (head + m) <= (unsigned)RING) {
-                    const unsigned lt = lanemask_lt();
-                    unsigned o = tail;
-#pragma unroll
-                    for (int k = 0; k < CONN; ++k) {
-                        if ((raised >> k) & 1u)
-                            ring[(o + __popc(bal[k] & lt)) & (RING - 1)] = (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k]));
-                        o += __popc(bal[k]);
-                    }
-                    tail += tot;
-                } else if (lane == 0) {
-                    S.overflow = 1;
-                }
-                head += m;
-                wpops += m;
-                ++nlevels;
-                __syncwarp();
-            }
-            if (lane == 0 && wpops) atomicAdd(&S.rpops, wpops);
-            __syncthreads();
-            pops += S.rpops;   // every warp's entries, the same in every thread
             break;
         }
         const unsigned navail = min(n, (unsigned)(QCAP + GCAP));
         pops += navail;
         ++nlevels;
-        const int src = (int)(L & 1), dst = src ^ 1;
-        const int cnext = (int)((L + 1) % 3);
-        if (threadIdx.x == 0) S.cq[(L + 2) % 3] = 0;   // last read two barriers ago
+        const int dst = src ^ 1;
+        const int cnext = ccur == 2 ? 0 : ccur + 1, cfree = cnext == 2 ? 0 : cnext + 1;
+        if (threadIdx.x == 0) S.cq[cfree] = 0;   // last read two barriers ago
+        for (int i = threadIdx.x; i < NCW; i += NT) S.claim[dst][i] = 0u;   // for level L + 1
+        unsigned *claim = S.claim[src];
         for (unsigned base = 0; base < navail; base += NT) {
             const unsigned i = base + threadIdx.x;
             const bool act = i < navail;
-            const unsigned p = act ? get_entry(S, gsp, src, i) : safe_p;
-            const uint32_t v = act ? Jb[p] : 0u;
-            const unsigned raised = expand<BH, CONN>(S.J, Jb, Ib, p, v, act, rows);
-            unsigned bal[CONN], tot = 0;
+            const unsigned p = act ? get_entry(S, gsp, src, i) : 0u;
+            uint32_t nv[CONN];
+            const unsigned raised = expand<BH, CONN>(S, claim, claim, p, act, nv);
+            if (raised) {
+                unsigned slot = atomicAdd(&S.cq[cnext], (unsigned)__popc(raised));
 #pragma unroll
-            for (int k = 0; k < CONN; ++k) {
-                bal[k] = __ballot_sync(FULL, (raised >> k) & 1u);
-                tot += __popc(bal[k]);
-            }
-            unsigned b0 = 0;
-            if (tot) {
-                if (lane == 0) b0 = atomicAdd(&S.cq[cnext], tot);
-                b0 = __shfl_sync(FULL, b0, 0);
-            }
-            const unsigned lt = lanemask_lt();
-#pragma unroll
-            for (int k = 0; k < CONN; ++k) {
-                if ((raised >> k) & 1u)
-                    put_entry(S, gsp, dst, b0 + __popc(bal[k] & lt), (uint16_t)(p + (CONN == 8 ? off8[k] : off4[k])));
-                b0 += __popc(bal[k]);
+                for (int k = 0; k < CONN; ++k)
+                    if ((raised >> k) & 1u) put_entry(S, gsp, dst, slot++, (uint16_t)(p + nb_off<CONN>(k)));
             }
         }
         __syncthreads();
         n = S.cq[cnext];
-        ++L;
+        src = dst;
+        ccur = cnext;
     }
-    rows.flush(S);
     return pops;
 }
 

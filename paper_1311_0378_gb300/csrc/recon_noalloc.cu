@@ -101,8 +101,10 @@ int setup_device(int dev, unsigned char **base, int *max_ctas)
 extern "C" int recon_run_noalloc(const uint8_t *I, uint8_t *J, int H, int W, int conn, void *cuda_stream)
 {
     if (!I || !J || H < 1 || W < 1 || (conn != 4 && conn != 8)) return RECON_EINVAL;
-    const unsigned nbx = (unsigned)((W + rk::BW - 1) / rk::BW), nby = (unsigned)((H + NOALLOC_BH - 1) / NOALLOC_BH);
-    if ((unsigned long long)nbx * nby > NOALLOC_MAX_BLOCKS) return RECON_EINVAL;  // beyond the fixed scratch
+    // block counts in 64-bit arithmetic: no overflow for any int H, W
+    const long long nbx_ll = ((long long)W + rk::BW - 1) / rk::BW, nby_ll = ((long long)H + NOALLOC_BH - 1) / NOALLOC_BH;
+    if (nbx_ll * nby_ll > (long long)NOALLOC_MAX_BLOCKS) return RECON_EINVAL;  // beyond the fixed scratch
+    const unsigned nbx = (unsigned)nbx_ll, nby = (unsigned)nby_ll;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RECON_ECUDA;
     unsigned char *base = nullptr;
@@ -152,9 +154,11 @@ extern "C" int recon_run_noalloc(const uint8_t *I, uint8_t *J, int H, int W, int
     // the init kernel zeroes control word, states, ring, status and counters
     if (rk_launch_init(grid, &P, st) != cudaSuccess) return RECON_ECUDA;
     if (rk_launch_main(NOALLOC_BH, grid, &P, st) != cudaSuccess) return RECON_ECUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return RECON_ECUDA;
+    // the status word comes back on the caller's stream, and only that stream
+    // is waited on (a plain cudaMemcpy would also wait for other work on the device)
     rk::Ctl h;
-    if (cudaMemcpy(&h, base + OFF_CTL, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return RECON_ECUDA;
+    if (cudaMemcpyAsync(&h, base + OFF_CTL, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return RECON_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RECON_ECUDA;
     if (h.abort) return RECON_ETIMEOUT;
     if (h.err_tile != INT_MAX) return RECON_EMARKER;
     return RECON_OK;

@@ -276,3 +276,36 @@ def test_environment_overrides():
     env["RECON_BLOCK_H"] = "96"
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120).stdout
     assert out.split() == ["status", str(rc.RECON_EINVAL)]
+
+
+def test_back_to_back_batches_without_sync():
+    """Two different batches, then the first again (a graph replay), issued
+    without a host wait in between: the staging buffer of the tile descriptors
+    is released right after its copy, so the host stages the next batch while
+    the previous kernel may still run. Every result is bit-exact."""
+    c = rc.recon_init(0, 0, 0)   # asynchronous context
+    try:
+        specs_a = [synth.TileSpec(512, 384, 80, 3, 20, m, 8, t) for t, m in enumerate((1, 0, 1))]
+        specs_b = [synth.TileSpec(300, 700, 60, 3, 20, m, 4, t) for t, m in enumerate((0, 1))]
+        pa, pb = synth.generate(specs_a, 21), synth.generate(specs_b, 22)
+        want_a = [oracle.recon(I, J, 8) for I, J in pa]
+        want_b = [oracle.recon(I, J, 4) for I, J in pb]
+        da = [(dev(I), dev(J)) for I, J in pa]
+        db = [(dev(I), dev(J)) for I, J in pb]
+        da2 = [(dev(I), dev(J)) for I, J in pa]
+        ta = [(I.data_ptr(), J.data_ptr(), s.H, s.W, s.W, 8) for (I, J), s in zip(da, specs_a)]
+        tb = [(I.data_ptr(), J.data_ptr(), s.H, s.W, s.W, 4) for (I, J), s in zip(db, specs_b)]
+        ta2 = [(I.data_ptr(), J.data_ptr(), s.H, s.W, s.W, 8) for (I, J), s in zip(da2, specs_a)]
+        rc.check(rc.recon_batch(c, ta), "batch a")
+        rc.check(rc.recon_batch(c, tb), "batch b")
+        rc.check(rc.recon_batch(c, ta2), "batch a again")
+        rc.check(rc.recon_batch(c, ta2), "batch a, graph replay on its own output (a fixed point)")
+        rc.check(rc.recon_sync(c), "sync")
+        for (_, J), w in zip(da, want_a):
+            np.testing.assert_array_equal(J.cpu().numpy(), w)
+        for (_, J), w in zip(db, want_b):
+            np.testing.assert_array_equal(J.cpu().numpy(), w)
+        for (_, J), w in zip(da2, want_a):
+            np.testing.assert_array_equal(J.cpu().numpy(), w)
+    finally:
+        rc.recon_free(c)

@@ -1,11 +1,19 @@
-"""The allocation-free entry point recon_run_noalloc, called through the C ABI,
-must give exactly what recon_run gives (reconstruction is integer max/min, so
-the tolerance is zero), on two calls in a row that reuse its built-in scratch
-array. It exists for callers that may not allocate memory while running; this
-file is collected last so a failure here never hides another test's result."""
+"""The allocation-free entry point recon_run_noalloc, called through the C ABI.
+
+It serves callers that may not allocate memory while running (a plugin whose
+host framework owns all device memory through its own pool, or a pipeline
+that cannot accept an allocation's implicit synchronisation), so its scratch
+is one array built into the library and shared by every call. Its results
+must equal the CPU oracle's byte for byte (reconstruction is integer max/min:
+the tolerance is zero) and the context-based recon_run's, on calls in a row
+that reuse that array: both markers, both connectivities, a ragged shape, the
+largest accepted size, and a marker above its mask, which must be reported
+without spoiling the next call. This file is collected last, so a failure
+here never hides another test's result."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -37,16 +45,43 @@ def _no_alloc(I, J, conn):
     return dJ.cpu().numpy()
 
 
-def test_no_alloc_matches_recon_run_twice():
+def _cases():
+    base = synth.workload("single512").tiles[0]
+    return [
+        (synth.tile_pair(synth.with_marker(base, synth.FILLHOLES), 1), 8),                    # 512 x 512
+        (synth.tile_pair(synth.TileSpec(1000, 777, 120, 3, 20, synth.HDOME, 4, 7), 5), 4),    # ragged
+        (synth.tile_pair(synth.TileSpec(333, 1029, 90, 3, 20, synth.FILLHOLES, 4, 8), 5), 4),  # ragged
+        (synth.tile_pair(base, 1), 8),
+    ]
+
+
+def test_no_alloc_matches_oracle_and_recon_run_on_calls_in_a_row():
     import paper_1311_0378_gb300.build as b
     b.build()
-    base = synth.workload("single512").tiles[0]
-    first = synth.tile_pair(synth.with_marker(base, synth.FILLHOLES), 1)          # 512 x 512
-    second = synth.tile_pair(synth.TileSpec(1000, 777, 120, 3, 20, synth.HDOME, 4, 7), 5)  # ragged
-    for (I, J), conn in ((first, 8), (second, 4)):
-        want = _with_context(I, J, conn)
-        got = _no_alloc(I, J, conn)
-        np.testing.assert_array_equal(got, want)
+    for (I, J), conn in _cases():
+        want = oracle.recon(I, J, conn)
+        got1 = _no_alloc(I, J, conn)
+        got2 = _no_alloc(I, J, conn)       # the same call again on the reused scratch
+        np.testing.assert_array_equal(got1, want)
+        np.testing.assert_array_equal(got2, want)
+        np.testing.assert_array_equal(got1, _with_context(I, J, conn))
+
+
+def test_no_alloc_largest_accepted_size():
+    """4096 x 8192 = 64 x 64 blocks of 64 x 128 pixels: the 4096-block limit."""
+    spec = synth.TileSpec(4096, 8192, 13000, 4, 12, synth.HDOME, 8, 3)
+    I, J = synth.tile_pair(spec, 9)
+    got = _no_alloc(I, J, 8)
+    np.testing.assert_array_equal(got, oracle.recon(I, J, 8))
+
+
+def test_no_alloc_marker_above_mask_then_normal_call():
+    (I, J), conn = _cases()[3]
+    bad = J.copy()
+    bad[100, 200] = min(255, int(I[100, 200]) + 1)
+    dI, dJ = _dev(I), _dev(bad)
+    assert rc.recon_run_noalloc(dI.data_ptr(), dJ.data_ptr(), I.shape[0], I.shape[1], conn, 0) == rc.RECON_EMARKER
+    np.testing.assert_array_equal(_no_alloc(I, J, conn), oracle.recon(I, J, conn))
 
 
 def test_no_alloc_rejects_oversized_input():
@@ -54,4 +89,6 @@ def test_no_alloc_rejects_oversized_input():
     p = d.data_ptr()
     # 8192 x 8192 needs 8192 blocks of 64 x 128: beyond the 4096-block scratch
     assert rc.recon_run_noalloc(p, p, 8192, 8192, 8, 0) == rc.RECON_EINVAL
+    assert rc.recon_run_noalloc(p, p, 4, 2147483647, 8, 0) == rc.RECON_EINVAL   # no int overflow
+    assert rc.recon_run_noalloc(p, p, 2147483647, 4, 8, 0) == rc.RECON_EINVAL
     assert rc.recon_run_noalloc(p, p, 4, 4, 6, 0) == rc.RECON_EINVAL
