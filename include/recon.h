@@ -164,7 +164,7 @@ enum {
                                 host memory (read with recon_trace, even while running) */
     RECON_P_LAST_ABORT = 10, /* read-only: which device-side bound ran out in the last call
                                 (0 = none; 1 rerun, 2 overflow, 3 levels, 4 scans, 5 unused,
-                                6 notify, 7 ring slot, 8 idle wait, 9 ring push, 10 TMA) */
+                                6 notify, 7 unused, 8 idle wait, 9 ring push, 10 TMA) */
     RECON_P_REVISIT_SCANS = 11, /* scan pairs a block runs when revisited (after a neighbour
                                    raised its halo) before its queue phase; default 0 */
     RECON_P_SCAN_GAIN = 12,     /* default adaptive scan-to-queue switch: after its fixed scan

@@ -37,7 +37,8 @@ struct recon_ctx {
     long long wait_ns = 2000000000ll;
     // device scratch
     unsigned char *d_meta = nullptr; size_t cap_meta = 0;      // descriptors + order tables
-    unsigned *d_state = nullptr, *d_ring = nullptr; size_t cap_blocks = 0;
+    unsigned *d_state = nullptr; size_t cap_blocks = 0, cap_ring = 0;
+    unsigned long long *d_ring = nullptr;
     rk::Ctl *d_ctl = nullptr;
     int *d_tile_err = nullptr; rk::Work *d_work = nullptr; size_t cap_tiles = 0;
     uint16_t *d_spill = nullptr; size_t cap_spill_ctas = 0;
@@ -441,20 +442,24 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
         grid = std::max(1, occ) * c->sms;
     }
     // scratch: grow only between launches (nothing in flight uses the old buffers)
-    const bool need = c->cap_meta < bytes || c->cap_blocks < nblocks || c->cap_tiles < (size_t)n ||
-                      c->cap_spill_ctas < (size_t)grid || !c->d_state || !c->d_ring;
+    // ring slots: any number is correct (laps are tagged); this many keeps
+    // producers from waiting for an earlier lap's block to be taken
+    const size_t ring_cap = std::min<size_t>(2 * (size_t)nblocks + 2 * (size_t)grid, (size_t)1 << 31);
+    const bool need = c->cap_meta < bytes || c->cap_blocks < nblocks || c->cap_ring < ring_cap ||
+                      c->cap_tiles < (size_t)n || c->cap_spill_ctas < (size_t)grid || !c->d_state || !c->d_ring;
     if (need) {
         CK(cudaStreamSynchronize(c->stream));
         drop_graph(c);
         if ((rc = grow(&c->d_meta, &c->cap_meta, bytes))) return rc;
-        if (c->cap_blocks < nblocks || !c->d_state || !c->d_ring) {
+        if (c->cap_blocks < nblocks || c->cap_ring < ring_cap || !c->d_state || !c->d_ring) {
             size_t a = 0, b = 0;
             if (c->d_state) cudaFree(c->d_state);
             if (c->d_ring) cudaFree(c->d_ring);
-            c->d_state = nullptr; c->d_ring = nullptr; c->cap_blocks = 0;
+            c->d_state = nullptr; c->d_ring = nullptr; c->cap_blocks = 0; c->cap_ring = 0;
             if ((rc = grow(&c->d_state, &a, nblocks))) return rc;
-            if ((rc = grow(&c->d_ring, &b, nblocks))) return rc;
-            c->cap_blocks = std::min(a, b);
+            if ((rc = grow(&c->d_ring, &b, ring_cap))) return rc;
+            c->cap_blocks = a;
+            c->cap_ring = b;
         }
         if (c->cap_tiles < (size_t)n || !c->d_tile_err || !c->d_work) {
             size_t a = 0, b = 0;
@@ -485,6 +490,7 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
     P.nblocks = nblocks;
     P.state = c->d_state;
     P.ring = c->d_ring;
+    P.ring_cap = (unsigned)ring_cap;
     P.ctl = c->d_ctl;
     P.tile_err = c->d_tile_err;
     P.work = c->d_work;

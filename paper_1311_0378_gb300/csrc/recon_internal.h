@@ -62,7 +62,8 @@ struct Params {
     const unsigned *order_base;    // ntiles + 1 cumulative block counts in packing order
     unsigned nblocks;
     unsigned *state;               // per block
-    unsigned *ring;                // nblocks entries
+    unsigned long long *ring;      // ring_cap slots: state << 32 | block (see next_item)
+    unsigned ring_cap;             // ring slots
     Ctl *ctl;
     int *tile_err;                 // per tile status
     Work *work;                    // per tile counters
@@ -78,7 +79,7 @@ struct Params {
 // where-codes recorded in Ctl::abort when a bound runs out
 enum {
     AB_RERUN = 1, AB_OVERFLOW = 2, AB_LEVELS = 3, AB_SCANS = 4, /* 5: unused */ AB_NOTIFY = 6,
-    AB_RING = 7, AB_IDLE = 8, AB_PUSH = 9, AB_TMA = 10
+    /* 7: unused */ AB_IDLE = 8, AB_PUSH = 9, AB_TMA = 10
 };
 
 }  // namespace rk

@@ -117,15 +117,44 @@ __device__ __forceinline__ void trace(const Params &P, unsigned code, unsigned b
         P.trace[blockIdx.x * (NT / 32) + (threadIdx.x >> 5)] = (code << 24) | (b & 0xFFFFFFu);
 }
 
-// Appends block b to the ring of re-queued blocks (the caller already moved
-// its state from IDLE to queued and counted it as outstanding).
+// The ring of re-queued blocks. Position t (from the tail for producers,
+// from the head for consumers, one atomicAdd each) uses slot t % ring_cap in
+// lap L = t / ring_cap. A slot word holds state << 32 | block, with state
+// 4L + 0 (free for lap L), 4L + 1 (holds lap L's block) or 4L + 2 (lap L's
+// ticket was given up). Producer and consumer of a position each wait for
+// their own lap's state, so laps never mix, whatever the ring size.
+__device__ __forceinline__ unsigned long long slot_word(unsigned state, unsigned b)
+{
+    return ((unsigned long long)state << 32) | b;
+}
+
+// Appends block b to the ring (the caller already moved its state from IDLE
+// to queued and counted it as outstanding). If the position's ticket was
+// given up, the slot is freed for the next lap and b goes to a new position.
 __device__ void push_hot(const Params &P, unsigned b)
 {
-    unsigned long long t = atomicAdd(&P.ctl->tail, 1ull);
-    unsigned *slot = &P.ring[t % P.nblocks];
-    for (int it = 0; atomicCAS(slot, EMPTY, b) != EMPTY; ++it) {
-        if (it > (1 << 22)) { set_abort(P, AB_PUSH); return; }
-        __nanosleep(64);
+    for (int attempt = 0;; ++attempt) {
+        if (attempt > (1 << 20)) { set_abort(P, AB_PUSH); return; }
+        const unsigned long long t = atomicAdd(&P.ctl->tail, 1ull);
+        unsigned long long *slot = &P.ring[t % P.ring_cap];
+        const unsigned lap4 = (unsigned)(t / P.ring_cap) * 4u;
+        bool moved = false;
+        for (int it = 0; !moved; ++it) {
+            const unsigned long long w = *(volatile unsigned long long *)slot;
+            const unsigned st = (unsigned)(w >> 32);
+            if (st == lap4) {                 // free for this lap: publish b
+                if (atomicCAS(slot, w, slot_word(lap4 + 1, b)) == w) return;
+                continue;                     // the ticket holder gave it up meanwhile
+            }
+            if (st == lap4 + 2) {             // given up: free it for the next lap, move on
+                atomicExch(slot, slot_word(lap4 + 4, 0));
+                moved = true;
+                continue;
+            }
+            // an earlier lap's block not yet taken: wait for its consumer
+            if (it > (1 << 22)) { set_abort(P, AB_PUSH); return; }
+            __nanosleep(64);
+        }
     }
 }
 
@@ -159,31 +188,63 @@ __device__ void notify_block(const Params &P, unsigned a)
 #endif
 
 // Thread 0: next block to process, or EMPTY when all work is done / aborted.
+// Re-queued blocks are handed out by tickets (one atomicAdd on the ring head,
+// never retried, so hundreds of CTAs asking at once do not contend in a
+// compare-and-swap loop), taken only while the ring looks non-empty -- and,
+// while first-visit (cold) blocks remain, only while it holds more than a few
+// items. A ticket below the tail waits for its producer to publish the block.
+// A ticket at or past the tail (other CTAs took the last items first) waits
+// for a later push, unless cold blocks remain: then its holder gives it up
+// (the slot's state for this lap goes from free to given-up, so the producer
+// pushes that block again elsewhere) and takes a cold block. So a CTA never
+// runs a block while it holds a ticket, and no CTA waits while cold blocks
+// are left. When no block is queued or running, none can be pushed any more:
+// the CTA leaves, dropping an unserved ticket.
 __device__ unsigned next_item(const Params &P)
 {
+    constexpr unsigned long long RING_MIN = 4;   // below this, prefer cold blocks over a ticket
     Ctl *c = P.ctl;
     unsigned long long idle0 = 0;
     unsigned sleep = 32;
     for (;;) {
         if (*(volatile int *)&c->abort) return EMPTY;
-        unsigned long long h = *(volatile unsigned long long *)&c->head;
-        unsigned long long t = *(volatile unsigned long long *)&c->tail;
-        if (h < t) {
-            if (atomicCAS(&c->head, h, h + 1) == h) {
-                unsigned *slot = &P.ring[h % P.nblocks];
-                unsigned b;
-                for (int it = 0; (b = atomicExch(slot, EMPTY)) == EMPTY; ++it) {
-                    if (it > (1 << 22)) { set_abort(P, AB_RING); return EMPTY; }
-                    __nanosleep(32);
+        const unsigned long long h = *(volatile unsigned long long *)&c->head;
+        const unsigned long long t = *(volatile unsigned long long *)&c->tail;
+        const bool cold_left = *(volatile unsigned *)&c->cold < P.nblocks;
+        if (h < t && (!cold_left || t - h > RING_MIN)) {
+            const unsigned long long tk = atomicAdd(&c->head, 1ull);
+            unsigned long long *slot = &P.ring[tk % P.ring_cap];
+            const unsigned lap4 = (unsigned)(tk / P.ring_cap) * 4u;
+            unsigned wait = 32;
+            for (;;) {
+                const unsigned long long w = *(volatile unsigned long long *)slot;
+                if ((unsigned)(w >> 32) == lap4 + 1) {   // this lap's block: take it, free the slot
+                    atomicExch(slot, slot_word(lap4 + 4, 0));
+                    return (unsigned)w;
                 }
-                return b;
+                if (*(volatile int *)&c->abort) return EMPTY;
+                if (tk < *(volatile unsigned long long *)&c->tail) {
+                    __nanosleep(32);   // its producer is publishing the block
+                    continue;
+                }
+                if ((unsigned)(w >> 32) == lap4 && *(volatile unsigned *)&c->cold < P.nblocks) {
+                    // other work exists: give the ticket up (unless its block just arrived)
+                    if (atomicCAS(slot, w, slot_word(lap4 + 2, 0)) == w) break;
+                    continue;
+                }
+                if (*(volatile unsigned *)&c->outstanding == 0) return EMPTY;
+                const unsigned long long now = gtimer();
+                if (idle0 == 0) idle0 = now;
+                else if ((long long)(now - idle0) > P.wait_ns) { set_abort(P, AB_IDLE); return EMPTY; }
+                __nanosleep(wait);
+                if (wait < IDLE_SLEEP_MAX_NS) wait <<= 1;
             }
-            continue;
         }
         if (*(volatile unsigned *)&c->cold < P.nblocks) {
             unsigned k = atomicAdd(&c->cold, 1u);
             if (k < P.nblocks) return cold_block(P, k);
         }
+        if (*(volatile unsigned long long *)&c->head < *(volatile unsigned long long *)&c->tail) continue;
         if (*(volatile unsigned *)&c->outstanding == 0) return EMPTY;
         unsigned long long now = gtimer();
         if (idle0 == 0) idle0 = now;
@@ -1219,10 +1280,11 @@ __global__ void __launch_bounds__(NT, BH == 128 ? 4 : 6) recon_persistent(Params
 __global__ void recon_init_kernel(Params P)
 {
     const size_t n = P.nblocks;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         P.state[i] = 0u;
-        P.ring[i] = EMPTY;
-    }
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)P.ring_cap;
+         i += (size_t)gridDim.x * blockDim.x)
+        P.ring[i] = 0ull;   // state 0: free for lap 0
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)P.ntiles;
          i += (size_t)gridDim.x * blockDim.x) {
         P.tile_err[i] = 0;

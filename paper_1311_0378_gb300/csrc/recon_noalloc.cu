@@ -55,14 +55,15 @@ constexpr size_t OFF_ERR = 512;
 constexpr size_t OFF_WORK = 576;
 constexpr size_t OFF_STATE = 1024;
 constexpr size_t OFF_RING = OFF_STATE + 4 * NOALLOC_MAX_BLOCKS;
-constexpr size_t OFF_SPILL = 65536;
+constexpr size_t RING_SLOTS = 2 * NOALLOC_MAX_BLOCKS + 2 * NOALLOC_MAX_CTAS;   // 8-byte slots
+constexpr size_t OFF_SPILL = 131072;
 constexpr size_t SPILL_BYTES = (size_t)NOALLOC_MAX_CTAS * 2 * rk::GCAP * sizeof(uint16_t);
 constexpr size_t NOALLOC_BYTES = 11u << 20;
 
 static_assert(sizeof(rk::Ctl) <= OFF_DESC - OFF_CTL, "control word");
 static_assert(sizeof(rk::TileDesc) <= 64, "descriptor");
 static_assert(OFF_BASE + 8 <= OFF_ERR && OFF_WORK + sizeof(rk::Work) <= OFF_STATE, "layout");
-static_assert(OFF_RING + 4 * NOALLOC_MAX_BLOCKS <= OFF_SPILL, "state and ring");
+static_assert(OFF_RING % 8 == 0 && OFF_RING + 8 * RING_SLOTS <= OFF_SPILL, "state and ring");
 static_assert(OFF_SPILL + SPILL_BYTES <= NOALLOC_BYTES, "spill areas");
 
 }  // namespace
@@ -140,7 +141,8 @@ extern "C" int recon_run_noalloc(const uint8_t *I, uint8_t *J, int H, int W, int
     P.order_base = (const unsigned *)(base + OFF_BASE);
     P.nblocks = nbx * nby;
     P.state = (unsigned *)(base + OFF_STATE);
-    P.ring = (unsigned *)(base + OFF_RING);
+    P.ring = (unsigned long long *)(base + OFF_RING);
+    P.ring_cap = 2 * (nbx * nby) + 2 * (unsigned)grid;
     P.ctl = (rk::Ctl *)(base + OFF_CTL);
     P.tile_err = (int *)(base + OFF_ERR);
     P.work = (rk::Work *)(base + OFF_WORK);
