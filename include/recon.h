@@ -150,7 +150,7 @@ const char *recon_strerror(int status);
 
 /* Tunables (recon_set_param / recon_get_param). */
 enum {
-    RECON_P_BLOCK_H = 1,     /* block height in rows: 32, 64 or 128 (block width is 128) */
+    RECON_P_BLOCK_H = 1,     /* block height in rows: 32, 64, 128 (default) or 256 (block width is 128) */
     RECON_P_SWEEPS = 2,      /* default variant: scan pairs before the queue; -1 = scans only */
     RECON_P_GRID = 3,        /* CTAs of the persistent launch; 0 = SMs x occupancy */
     RECON_P_BANDS = 4,       /* warps that scan a block concurrently (1, 2 or 4) */
@@ -169,7 +169,7 @@ enum {
                                    raised its halo) before its queue phase; default 0 */
     RECON_P_SCAN_GAIN = 12,     /* default adaptive scan-to-queue switch: after its fixed scan
                                    pairs a block keeps scanning while a pair raises at least this
-                                   many pixels (first visits and revisits); 0 = off */
+                                   many pixels (first visits and revisits); 0 = off; default 2048 */
     RECON_P_TUNE_FROM_CACHE = 13 /* read-only: 1 if the last recon_autotune call took its
                                    result from the cache instead of timing trials */
 };
@@ -225,7 +225,7 @@ int recon_last_kernel_ms(recon_ctx *ctx, float *ms);
 int recon_run_noalloc(const uint8_t *I, uint8_t *J, int H, int W, int conn, void *cuda_stream);
 
 /* Autotuner: times every candidate block height {32, 64, 128} x bands
- * {2, 4} x first-visit scan pairs {0, 1, 2} x adaptive scan gain {0, 512} on
+ * {2, 4} x first-visit scan pairs {0, 1, 2} x adaptive scan gain {0, 2048} on
  * this batch (each `reps` times after one warm-up run, J restored from a
  * device backup before every run), installs the fastest in the context and
  * writes it to best[4] = {block height, bands, scan pairs, scan gain}. J

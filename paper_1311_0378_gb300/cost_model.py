@@ -283,8 +283,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--out", default=MODEL_PATH)
     ap.add_argument("--queue-k", type=int, default=1)
-    ap.add_argument("--scan-variant", type=int, default=1 + 256 * 8,
-                    help="variant A: 1 scan pair, then keep scanning while a pair raises >= 512 px")
+    ap.add_argument("--scan-variant", type=int, default=1 + 256 * 32,
+                    help="variant A: 1 scan pair, then keep scanning while a pair raises >= 2048 px")
     ap.add_argument("--eval", action="store_true", help="then compare learned vs plain on eval1000")
     ap.add_argument("--eval-only", action="store_true", help="only evaluate the model at --out")
     ap.add_argument("--data", help="reuse a labelled dataset (.npz written by an earlier run) instead of labelling")

@@ -33,7 +33,9 @@ struct recon_ctx {
     unsigned flags = 0;
     int sms = 0;
     // tunables
-    int bh = 128, k = 1, grid = 0, bands = 4, order_policy = 1, phantom = 0, use_tma = 1, revisit_scans = 0, scan_gain = 0;
+    // defaults: 128-row blocks, one scan pair on a first visit, then more pairs
+    // while a pair still raises >= 2048 pixels (first visits and revisits)
+    int bh = 128, k = 1, grid = 0, bands = 4, order_policy = 1, phantom = 0, use_tma = 1, revisit_scans = 0, scan_gain = 2048;
     long long wait_ns = 2000000000ll;
     // device scratch
     unsigned char *d_meta = nullptr; size_t cap_meta = 0;      // descriptors + order tables
@@ -130,7 +132,7 @@ extern "C" int recon_init(recon_ctx **out, int device, void *cuda_stream, unsign
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_ctl, sizeof(rk::Ctl));
     if (e == cudaSuccess) {
         int occ = 0;
-        for (int bh : {32, 64, 128})
+        for (int bh : {32, 64, 128, 256})
             if (e == cudaSuccess) e = rk_configure(bh, &occ);
     }
     if (e != cudaSuccess) {
@@ -214,7 +216,7 @@ extern "C" int recon_set_param(recon_ctx *c, int key, int64_t v)
     if (!c) return RECON_EINVAL;
     switch (key) {
     case RECON_P_BLOCK_H:
-        if (v != 32 && v != 64 && v != 128) return RECON_EINVAL;
+        if (v != 32 && v != 64 && v != 128 && v != 256) return RECON_EINVAL;
         c->bh = (int)v; break;
     case RECON_P_SWEEPS:
         if (v < -1 || v > 64) return RECON_EINVAL;
@@ -309,7 +311,10 @@ static int encode_map(CUtensorMap *m, const void *base, int H, int W, int pitch,
     if (!fn) return 0;
     cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
     cuuint64_t strides[1] = {(cuuint64_t)pitch};
-    cuuint32_t box[2] = {(cuuint32_t)rk::BOXW, (cuuint32_t)(bh + 2)};
+    // at most 256 rows per box: taller blocks are loaded as two boxes whose
+    // height is a multiple of 4 rows (the kernel's Boxes<BH>)
+    const int rows = bh + 2 > 256 ? ((bh + 2) / 2 + 3) / 4 * 4 : bh + 2;
+    cuuint32_t box[2] = {(cuuint32_t)rk::BOXW, (cuuint32_t)rows};
     cuuint32_t es[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -903,7 +908,7 @@ extern "C" int recon_autotune_cache_load(recon_ctx *c, const int *entries, int c
     if (!c || count < 0 || (count > 0 && !entries)) return RECON_EINVAL;
     for (int i = 0; i < count; ++i) {
         const int *e = entries + 7 * i;
-        if ((e[3] != 32 && e[3] != 64 && e[3] != 128) || (e[4] != 1 && e[4] != 2 && e[4] != 4) || e[5] < -1 ||
+        if ((e[3] != 32 && e[3] != 64 && e[3] != 128 && e[3] != 256) || (e[4] != 1 && e[4] != 2 && e[4] != 4) || e[5] < -1 ||
             e[5] > 64 || e[6] < 0 || e[6] > (1 << 20) || e[1] < 1 || e[1] > 3 || (e[2] != 0 && e[2] != 1))
             return RECON_EINVAL;
     }
@@ -953,7 +958,7 @@ extern "C" int recon_autotune(recon_ctx *c, const recon_tile *tiles, int n, int 
     float best_ms = 1e30f;
     int bb[4] = {save_bh, save_bands, save_k, save_gain};
     int rc = RECON_OK;
-    const int BHs[3] = {32, 64, 128}, BANDS[2] = {2, 4}, KS[3] = {0, 1, 2}, GAINS[2] = {0, 512};
+    const int BHs[3] = {32, 64, 128}, BANDS[2] = {2, 4}, KS[3] = {0, 1, 2}, GAINS[2] = {0, 2048};
     for (int a = 0; a < 3 && e == cudaSuccess && rc == RECON_OK; ++a)
         for (int b = 0; b < 2 && e == cudaSuccess && rc == RECON_OK; ++b)
             for (int k = 0; k < 3 && e == cudaSuccess && rc == RECON_OK; ++k)

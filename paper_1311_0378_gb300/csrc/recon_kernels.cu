@@ -62,10 +62,22 @@ __device__ __forceinline__ unsigned long long gtimer()
 }
 
 
+// Rows of a block held in shared memory: BH + 2 (with the halo), loaded by
+// one TMA box -- or, above 256 rows (the largest box), by two boxes of TBOX
+// rows, TBOX a multiple of 4 so that the second box starts 128-byte aligned;
+// the rows past the halo row are loaded but never used.
+template <int BH>
+struct Boxes {
+    static constexpr int N = BH + 2 > 256 ? 2 : 1;
+    static constexpr int TBOX = N == 1 ? BH + 2 : ((BH + 2) / 2 + 3) / 4 * 4;
+    static constexpr int ROWS = N * TBOX;
+    static_assert(TBOX <= 256 && ROWS >= BH + 2 && (TBOX * BOXW) % 128 == 0 || N == 1, "TMA boxes");
+};
+
 template <int BH>
 struct Smem {
-    alignas(128) uint32_t J[(BH + 2) * PW];   // TMA destinations: 128-byte aligned
-    alignas(128) uint32_t I[(BH + 2) * PW];   // 0 on the halo: nothing ever propagates into it
+    alignas(128) uint32_t J[Boxes<BH>::ROWS * PW];   // TMA destinations: 128-byte aligned
+    alignas(128) uint32_t I[Boxes<BH>::ROWS * PW];   // 0 on the halo: nothing ever propagates into it
     unsigned long long mbar;                  // TMA completion barrier
     uint16_t q[2][QCAP];          // BFS levels (byte offsets into J)
     uint8_t hIt[BW + 2], hIb[BW + 2];  // halo mask, top / bottom rows, x = -1 .. BW
@@ -75,6 +87,7 @@ struct Smem {
     unsigned pairmask[BH / 32];   // rows changed by the latest scan pair
     unsigned claim[2][BH * BW / 32];  // wavefront ownership bits, one per interior pixel, by level parity
     unsigned cq[3];               // level sizes, rotating by level (see run_queue)
+    unsigned solo_src, solo_L;    // queue buffer and level count after a warp-solo run
     unsigned item, tile, flag, overflow, notify, visited;
     unsigned phase;               // parity of the TMA barrier's next completion
     unsigned abrt;                // block-uniform copy of the abort word
@@ -314,13 +327,18 @@ __device__ void tma_load_block(Smem<BH> &S, const Params &P, const TileDesc &D, 
         // of global memory as well as of this CTA's shared memory.
         asm volatile("fence.proxy.async.global;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const unsigned bytes = 2u * (unsigned)((BH + 2) * BOXW);
+        const unsigned bytes = 2u * (unsigned)(Boxes<BH>::ROWS * BOXW);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
         const int cx = x0 - XOFF, cy = y0 - 1;
-        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-                     :: "r"(smem_addr(S.J)), "l"(mJ), "r"(cx), "r"(cy), "r"(bar) : "memory");
-        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-                     :: "r"(smem_addr(S.I)), "l"(mI), "r"(cx), "r"(cy), "r"(bar) : "memory");
+        constexpr int NBOX = Boxes<BH>::N, TBOX = Boxes<BH>::TBOX;
+#pragma unroll
+        for (int bx = 0; bx < NBOX; ++bx) {
+            const unsigned so = (unsigned)(bx * TBOX * BOXW);
+            asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                         :: "r"(smem_addr(S.J) + so), "l"(mJ), "r"(cx), "r"(cy + bx * TBOX), "r"(bar) : "memory");
+            asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                         :: "r"(smem_addr(S.I) + so), "l"(mI), "r"(cx), "r"(cy + bx * TBOX), "r"(bar) : "memory");
+        }
     }
     const unsigned ph = S.phase;
     unsigned done = 0;
@@ -798,17 +816,18 @@ __device__ __forceinline__ uint32_t max3u(uint32_t a, uint32_t b, uint32_t c) { 
 // the next frontier and offers its value again.
 // The maxima of all directions come from a 5 x 5 window of J around p held in
 // registers: the 3 x 3 centre is read for the propagation test, the outer
-// ring only when this thread owns a candidate. Returns the raised neighbours
-// (bit k) with their new values in nv[k].
+// ring when p has a candidate. Returns the raised neighbours
+// (bit k) with their new values in nv[k]; `own` gets the candidates this
+// thread claimed.
 template <int BH, int CONN>
-__device__ __forceinline__ unsigned expand(Smem<BH> &S, const unsigned *claim_ro, unsigned *claim, unsigned p,
-                                           bool act, uint32_t (&nv)[CONN])
+__device__ __forceinline__ unsigned expand(Smem<BH> &S, unsigned *claim, unsigned p, bool act,
+                                           uint32_t (&nv)[CONN], unsigned &own)
 {
     constexpr int RB = PW * 4;
     const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
     volatile uint8_t *Jm = (volatile uint8_t *)S.J;
     const uint8_t *Ib = (const uint8_t *)S.I;
-    (void)claim_ro;
+    own = 0;
 #ifdef RECON_CHECKS
     // an interior pixel of the block: rows 1 .. BH of J, columns XOFF .. XOFF + BW - 1
     if (act && !RK_CHECK(p >= (unsigned)RB && p < (unsigned)((BH + 1) * RB) && (unsigned)(p % RB - XOFF) < (unsigned)BW,
@@ -837,16 +856,10 @@ __device__ __forceinline__ unsigned expand(Smem<BH> &S, const unsigned *claim_ro
         const int qb = pb + nb_dy<CONN>(k) * BW + nb_dx<CONN>(k);
         old[k] = ((cand >> k) & 1u) ? atomicOr(&claim[qb >> 5], 1u << (qb & 31)) : ~0u;
     }
-    unsigned own = 0;
-#pragma unroll
-    for (int k = 0; k < CONN; ++k) {
-        const int qb = pb + nb_dy<CONN>(k) * BW + nb_dx<CONN>(k);
-        own |= ((old[k] >> (qb & 31)) & 1u) ? 0u : (1u << k);
-    }
-    if (!own) return 0;
-    // outer ring of the 5 x 5 window; rows p - 2 and p + 2 exist only for
-    // rows 2 .. BH - 1 (elsewhere they are needed only for halo pixels, which
-    // are never owned, so a valid row is read in their place)
+    // outer ring of the 5 x 5 window, read while the claims are in flight;
+    // rows p - 2 and p + 2 exist only for rows 2 .. BH - 1 (elsewhere they are
+    // needed only for halo pixels, which are never owned, so a valid row is
+    // read in their place)
     const unsigned um = r >= 2 ? p - 2 * RB : p - RB, dm = r <= BH - 1 ? p + 2 * RB : p + RB;
     uint32_t M[CONN];
     if (CONN == 8) {
@@ -877,6 +890,11 @@ __device__ __forceinline__ unsigned expand(Smem<BH> &S, const unsigned *claim_ro
         M[2] = max(max3u(e2, ne, se), v);   // q = E
         M[3] = max(max3u(s2, sw, se), v);   // q = S
     }
+#pragma unroll
+    for (int k = 0; k < CONN; ++k) {
+        const int qb = pb + nb_dy<CONN>(k) * BW + nb_dx<CONN>(k);
+        own |= ((old[k] >> (qb & 31)) & 1u) ? 0u : (1u << k);
+    }
     unsigned raised = 0;
 #pragma unroll
     for (int k = 0; k < CONN; ++k) {
@@ -906,12 +924,15 @@ __device__ __forceinline__ unsigned expand(Smem<BH> &S, const unsigned *claim_ro
 // claim[L % 2]; the other bitmap, last used by level L - 1, is cleared during
 // level L for level L + 1. n0 = size of level 0 (counted in cq[0]; the seeding
 // pass zeroed cq[1], cq[2]). Returns entries processed.
+constexpr unsigned SOLO_MAX = 32;   // levels this small run in warp 0 alone
+
 template <int BH, int CONN>
 __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *gsp, unsigned n0,
                                         unsigned long long &nlevels)
 {
     constexpr unsigned MAX_LEVELS = 1u << 21;
     constexpr int NCW = BH * BW / 32;   // claim words per bitmap
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long pops = 0;
     for (int i = threadIdx.x; i < 2 * NCW; i += NT) (&S.claim[0][0])[i] = 0u;
     __syncthreads();
@@ -921,6 +942,71 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
         if (L > MAX_LEVELS) {
             if (threadIdx.x == 0) set_abort(P, AB_LEVELS);
             break;
+        }
+        if (n <= SOLO_MAX) {
+            // Thin wavefront: warp 0 runs the levels alone, one pixel per
+            // lane, with __syncwarp as the level barrier, while the other
+            // warps wait at one CTA barrier. Claims go to one bitmap and each
+            // owner releases its bits after the level; slots of the next
+            // level come from ballots. When a level outgrows the warp, the
+            // CTA takes it over.
+            if (warp == 0) {
+                for (int i = lane; i < NCW; i += 32) S.claim[src ^ 1][i] = 0u;
+                __syncwarp();
+                unsigned *claim = S.claim[src];
+                unsigned m = n;
+                int s = src;
+                while (m > 0 && m <= SOLO_MAX) {
+                    if (++L > MAX_LEVELS) {
+                        if (lane == 0) set_abort(P, AB_LEVELS);
+                        m = 0;
+                        break;
+                    }
+                    pops += m;
+                    ++nlevels;
+                    const bool act = (unsigned)lane < m;
+                    const unsigned p = act ? get_entry(S, gsp, s, lane) : 0u;
+                    uint32_t nv[CONN];
+                    unsigned own;
+                    const unsigned raised = expand<BH, CONN>(S, claim, p, act, nv, own);
+                    const unsigned lt = lanemask_lt();
+                    unsigned tot = 0;
+#pragma unroll
+                    for (int k = 0; k < CONN; ++k) {
+                        const unsigned bk = __ballot_sync(FULL, (raised >> k) & 1u);
+                        if ((raised >> k) & 1u) put_entry(S, gsp, s ^ 1, tot + __popc(bk & lt), (uint16_t)(p + nb_off<CONN>(k)));
+                        tot += __popc(bk);
+                    }
+                    __syncwarp();
+                    if (own) {   // release this level's claims
+                        constexpr int RB = PW * 4;
+                        const int r = (int)(p / (unsigned)RB), x = (int)p - r * RB - XOFF;
+                        const int pb = (r - 1) * BW + x;
+#pragma unroll
+                        for (int k = 0; k < CONN; ++k)
+                            if ((own >> k) & 1u) {
+                                const int qb = pb + nb_dy<CONN>(k) * BW + nb_dx<CONN>(k);
+                                atomicAnd(&claim[qb >> 5], ~(1u << (qb & 31)));
+                            }
+                    }
+                    __syncwarp();
+                    m = tot;
+                    s ^= 1;
+                }
+                if (lane == 0) {
+                    S.cq[0] = m;
+                    S.cq[1] = 0;
+                    S.cq[2] = 0;
+                    S.solo_src = (unsigned)s;
+                    S.solo_L = L;
+                }
+            }
+            __syncthreads();
+            n = S.cq[0];
+            src = (int)S.solo_src;
+            ccur = 0;
+            L = S.solo_L;   // the same in every thread
+            continue;
         }
         const unsigned navail = min(n, (unsigned)(QCAP + GCAP));
         pops += navail;
@@ -935,7 +1021,8 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
             const bool act = i < navail;
             const unsigned p = act ? get_entry(S, gsp, src, i) : 0u;
             uint32_t nv[CONN];
-            const unsigned raised = expand<BH, CONN>(S, claim, claim, p, act, nv);
+            unsigned own;
+            const unsigned raised = expand<BH, CONN>(S, claim, p, act, nv, own);
             if (raised) {
                 unsigned slot = atomicAdd(&S.cq[cnext], (unsigned)__popc(raised));
 #pragma unroll
@@ -1190,7 +1277,7 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
 }
 
 template <int BH>
-__global__ void __launch_bounds__(NT, BH == 128 ? 4 : 6) recon_persistent(Params P)
+__global__ void __launch_bounds__(NT, BH == 256 ? 2 : (BH == 128 ? 4 : 6)) recon_persistent(Params P)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<BH> &S = *reinterpret_cast<Smem<BH> *>(smem_raw);
@@ -1346,6 +1433,7 @@ extern "C" size_t rk_smem_bytes(int bh)
     case 32: return sizeof(rk::Smem<32>);
     case 64: return sizeof(rk::Smem<64>);
     case 128: return sizeof(rk::Smem<128>);
+    case 256: return sizeof(rk::Smem<256>);
     }
     return 0;
 }
@@ -1357,6 +1445,7 @@ extern "C" cudaError_t rk_configure(int bh, int *ctas_per_sm)
     case 32: fn = (const void *)rk::recon_persistent<32>; break;
     case 64: fn = (const void *)rk::recon_persistent<64>; break;
     case 128: fn = (const void *)rk::recon_persistent<128>; break;
+    case 256: fn = (const void *)rk::recon_persistent<256>; break;
     default: return cudaErrorInvalidValue;
     }
     const size_t sm = rk_smem_bytes(bh);
@@ -1411,6 +1500,7 @@ extern "C" cudaError_t rk_launch_main(int bh, int grid, const rk::Params *P, cud
     case 32: rk::recon_persistent<32><<<grid, rk::NT, sm, st>>>(*P); break;
     case 64: rk::recon_persistent<64><<<grid, rk::NT, sm, st>>>(*P); break;
     case 128: rk::recon_persistent<128><<<grid, rk::NT, sm, st>>>(*P); break;
+    case 256: rk::recon_persistent<256><<<grid, rk::NT, sm, st>>>(*P); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -1,7 +1,9 @@
-// Batch scheduler: the learned cost model picks each tile's variant (scans to
-// stability vs scans + queue) and the packing order (decreasing predicted
-// cost). Its outputs only reorder and re-parameterise work; pixel values are
-// never touched, and without a model the plain schedule applies.
+// Batch scheduler: the learned cost model picks each tile's variant (two scan
+// / queue settings) and orders tiles of equal size by decreasing predicted
+// cost; tiles of different sizes go largest first (on 1000-tile batches,
+// ordering by predicted cost alone was 2-4% slower than by area). Its outputs
+// only reorder and re-parameterise work; pixel values are never touched, and
+// without a model the plain schedule applies.
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -113,6 +115,9 @@ int recon_sched_plan(recon_sched *s, const recon_tile *tiles, int n, int sms, cu
         cost[t] = a < b ? a : b;
     }
     std::iota(order->begin(), order->end(), 0);
-    std::stable_sort(order->begin(), order->end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::stable_sort(order->begin(), order->end(), [&](int x, int y) {
+        const long long ax = (long long)tiles[x].H * tiles[x].W, ay = (long long)tiles[y].H * tiles[y].W;
+        return ax != ay ? ax > ay : cost[x] > cost[y];
+    });
     return RECON_OK;
 }

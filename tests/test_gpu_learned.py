@@ -19,7 +19,7 @@ from paper_1311_0378_gb300 import cost_model  # noqa: E402
 def test_model_file_meta():
     theta, norm, variants, meta = cost_model.load()
     assert theta.shape == (rc.RECON_MLP_NPARAMS,) and np.isfinite(theta).all()
-    assert meta["tiles"] == 20000 and variants == (1 + 256 * 8, 1)
+    assert meta["tiles"] == 20000 and variants == (1 + 256 * 32, 1)
 
 
 def test_learned_schedule_gain_and_identity():
