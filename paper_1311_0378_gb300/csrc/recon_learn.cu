@@ -13,6 +13,7 @@
 //   mlp_grad         forward + backward of L = 1/(2N) sum (Y - T)^2 over a
 //                    mini-batch, gradients accumulated per CTA in shared memory
 //   adam_kernel      Adam update (Kingma & Ba 2015, Algorithm 1); zeroes the gradient
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "recon_learn.h"
@@ -22,6 +23,7 @@ namespace rl {
 struct FeatTile {
     const uint8_t *I, *J;
     int H, W, pitch, op;
+    int crow;   // rows per chunk (about CHUNK_PX pixels)
 };
 
 __device__ __forceinline__ int find_chunk_tile(const unsigned *chunk_base, int n, unsigned c)
@@ -36,24 +38,61 @@ __device__ __forceinline__ int find_chunk_tile(const unsigned *chunk_base, int n
 
 // counts: per tile NCOUNT u32: [0..15] histogram, [16] bright, [17] zero J, [18] violations
 constexpr int NCOUNT = 19;
-constexpr int CHUNK_ROWS = 16;
+constexpr int CHUNK_PX = 1 << 16;   // pixels per chunk of a tile (a whole number of rows, at least one)
 
-// Adds one pixel to the per-thread counts. The bin is matched against every
-// constant index so the counts stay in registers. op: the tile's operation
-// (0 dilation, 1 erosion, 2 FillHoles), see the header comment.
-__device__ __forceinline__ void count(unsigned (&loc)[NCOUNT], uint32_t i, uint32_t j, int op)
-{
-    if (op != 0) {
-        i ^= 0xFFu;
-        j = (op == 2) ? 0u : (j ^ 0xFFu);
-    }
-    const uint32_t bin = (j > i) ? 18u : ((i - j) >> 4);
+// Per-thread counts. The 16 histogram bins are one-hot counters in 8-bit
+// fields of two 64-bit words (bins 0-7 and 8-15: one shift and two adds per
+// pixel), moved into the 32-bit totals at least every 255 pixels; blob pixels,
+// zero markers and J > I violations are plain counters.
+struct Counts {
+    unsigned long long lo = 0, hi = 0;   // 8-bit fields: bins 0..7, 8..15
+    unsigned tot[NCOUNT] = {};
+    unsigned pend = 0;                   // pixels in the 8-bit fields
+
+    __device__ __forceinline__ void flush()
+    {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) loc[k] += (bin == (uint32_t)k);
-    loc[18] += (bin == 18u);
-    loc[16] += (i >= 100);
-    loc[17] += (j == 0);
-}
+        for (int k = 0; k < 8; ++k) {
+            tot[k] += (unsigned)(lo >> (8 * k)) & 0xFFu;
+            tot[8 + k] += (unsigned)(hi >> (8 * k)) & 0xFFu;
+        }
+        lo = hi = 0;
+        pend = 0;
+    }
+    // one pixel; op: the tile's operation (0 dilation, 1 erosion, 2 FillHoles)
+    __device__ __forceinline__ void add(uint32_t i, uint32_t j, int op)
+    {
+        if (op != 0) {
+            i ^= 0xFFu;
+            j = (op == 2) ? 0u : (j ^ 0xFFu);
+        }
+        const bool bad = j > i;
+        const uint32_t bin = (i - j) >> 4;   // 0..15 unless bad
+        const unsigned long long one = bad ? 0ull : (1ull << (8 * (bin & 7)));
+        lo += bin < 8 ? one : 0ull;
+        hi += bin < 8 ? 0ull : one;
+        tot[18] += bad;
+        tot[16] += (i >= 100);
+        tot[17] += (j == 0);
+    }
+    // 16 pixels from one 16-byte vector of I and of J (<= 255 pixels pending)
+    __device__ __forceinline__ void add16(uint4 a, uint4 b, int op)
+    {
+        if (pend > 255 - 16) flush();
+        const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) add((aw[q] >> (8 * s)) & 0xFF, (bw[q] >> (8 * s)) & 0xFF, op);
+        pend += 16;
+    }
+    __device__ __forceinline__ void add1(uint32_t i, uint32_t j, int op)
+    {
+        if (pend > 254) flush();
+        add(i, j, op);
+        pend += 1;
+    }
+};
 
 __global__ void __launch_bounds__(256) features_kernel(const FeatTile *T, int n, const unsigned *chunk_base,
                                                        unsigned nchunks, unsigned *counts)
@@ -64,39 +103,31 @@ __global__ void __launch_bounds__(256) features_kernel(const FeatTile *T, int n,
         __syncthreads();
         const int t = find_chunk_tile(chunk_base, n, c);
         const FeatTile d = T[t];
-        const int y0 = (int)(c - chunk_base[t]) * CHUNK_ROWS;
-        const int y1 = min(d.H, y0 + CHUNK_ROWS);
-        unsigned loc[NCOUNT];
-#pragma unroll
-        for (int k = 0; k < NCOUNT; ++k) loc[k] = 0;
+        const int y0 = (int)(c - chunk_base[t]) * d.crow;
+        const int rows = min(d.H, y0 + d.crow) - y0;
+        Counts loc;
         const bool vec = ((d.pitch & 15) == 0) && (((uintptr_t)d.I & 15) == 0) && (((uintptr_t)d.J & 15) == 0);
-        for (int y = y0; y < y1; ++y) {
-            const uint8_t *ri = d.I + (size_t)y * d.pitch, *rj = d.J + (size_t)y * d.pitch;
-            if (vec) {
-                const int nv = d.W >> 4;
-                for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-                    const uint4 a = __ldg((const uint4 *)ri + v), b = __ldg((const uint4 *)rj + v);
-                    const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-#pragma unroll
-                        for (int s = 0; s < 4; ++s) {
-                            const uint32_t i = (aw[q] >> (8 * s)) & 0xFF, j = (bw[q] >> (8 * s)) & 0xFF;
-                            count(loc, i, j, d.op);
-                        }
-                }
-                for (int x = (nv << 4) + threadIdx.x; x < d.W; x += blockDim.x) {
-                    count(loc, ri[x], rj[x], d.op);
-                }
-            } else {
-                for (int x = threadIdx.x; x < d.W; x += blockDim.x) {
-                    count(loc, ri[x], rj[x], d.op);
-                }
-            }
+        // every thread strides over the chunk's 16-byte vectors (rows x W/16),
+        // so narrow tiles keep the whole CTA busy and each thread has several
+        // loads in flight; the ragged column tail and unaligned tiles go byte by byte
+        const int nv = vec ? d.W >> 4 : 0;
+        const int nvec = rows * nv;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < nvec; e += blockDim.x) {
+            const int r = e / nv, v = e - r * nv;
+            const size_t o = (size_t)(y0 + r) * d.pitch;
+            loc.add16(__ldg((const uint4 *)(d.I + o) + v), __ldg((const uint4 *)(d.J + o) + v), d.op);
         }
+        const int tw = d.W - 16 * nv;   // pixels per row not covered by vectors
+        for (int e = threadIdx.x; e < rows * tw; e += blockDim.x) {
+            const int r = e / tw, x = 16 * nv + (e - r * tw);
+            const size_t o = (size_t)(y0 + r) * d.pitch + x;
+            loc.add1(d.I[o], d.J[o], d.op);
+        }
+        loc.flush();
 #pragma unroll
         for (int k = 0; k < NCOUNT; ++k)
-            if (loc[k]) atomicAdd(&sh[k], loc[k]);
+            if (loc.tot[k]) atomicAdd(&sh[k], loc.tot[k]);
         __syncthreads();
         if (threadIdx.x < NCOUNT && sh[threadIdx.x]) atomicAdd(&counts[t * NCOUNT + threadIdx.x], sh[threadIdx.x]);
         __syncthreads();
@@ -246,8 +277,9 @@ cudaError_t rl_features(const rl_tile *tiles, int n, void *scratch, size_t scrat
     for (int t = 0; t < n; ++t) {
         F[t].I = tiles[t].I; F[t].J = tiles[t].J; F[t].H = tiles[t].H; F[t].W = tiles[t].W;
         F[t].pitch = tiles[t].pitch; F[t].op = tiles[t].op;
+        F[t].crow = std::max(1, std::min(tiles[t].H, rl::CHUNK_PX / std::max(tiles[t].W, 1)));
         base[t] = acc;
-        acc += (unsigned)((tiles[t].H + rl::CHUNK_ROWS - 1) / rl::CHUNK_ROWS);
+        acc += (unsigned)((tiles[t].H + F[t].crow - 1) / F[t].crow);
     }
     base[n] = acc;
     unsigned char *d = (unsigned char *)scratch;
