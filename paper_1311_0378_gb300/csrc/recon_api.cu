@@ -26,6 +26,8 @@ extern "C" cudaError_t rk_launch_init(int grid, const rk::Params *P, cudaStream_
 extern "C" cudaError_t rk_launch_main(int bh, int grid, const rk::Params *P, cudaStream_t st);
 extern "C" cudaError_t rk_launch_fill(const rk::TileDesc *tiles, const int *list, int nlist, cudaStream_t st);
 
+constexpr int HOST_SEGMENTS = 4;   // pipeline segments of the end-to-end (host buffer) calls
+
 struct recon_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -47,12 +49,15 @@ struct recon_ctx {
     // host staging (pinned)
     unsigned char *h_meta = nullptr; size_t cap_hmeta = 0;
     cudaEvent_t meta_free = nullptr, ev0 = nullptr, ev1 = nullptr;
-    // end-to-end buffers
+    // end-to-end buffers and the copy streams of its pipeline
     uint8_t *d_img = nullptr; size_t cap_img = 0;
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_in[HOST_SEGMENTS] = {};
     // last call
     int last_n = 0;
     int launched = 0;
     int last_err_tile = -1;
+    int err_tile_base = 0;   // index in the caller's batch of the last launch's first tile
     int last_abort = 0;
     // diagnostics: per-warp progress words in mapped host memory
     unsigned *h_trace = nullptr; unsigned *d_trace = nullptr; size_t cap_trace = 0; int trace_on = 0;
@@ -183,6 +188,10 @@ extern "C" int recon_free(recon_ctx *c)
     if (c->meta_free) cudaEventDestroy(c->meta_free);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    for (int s = 0; s < HOST_SEGMENTS; ++s)
+        if (c->ev_in[s]) cudaEventDestroy(c->ev_in[s]);
+    if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+    if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     recon_sched_destroy(c->sched);
     delete c;
@@ -531,6 +540,7 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
 
     c->last_n = n;
     c->last_err_tile = -1;
+    c->err_tile_base = 0;
     const bool use_graph = !(c->flags & RECON_FLAG_NO_GRAPH);
     if (use_graph && c->gexec && sig == c->gsig) {
         // the graph records meta_free itself, right after its descriptor copy
@@ -599,7 +609,7 @@ extern "C" int recon_sync(recon_ctx *c)
     if (!c->launched) return RECON_OK;
     rk::Ctl h;
     CK(cudaMemcpy(&h, c->d_ctl, sizeof(h), cudaMemcpyDeviceToHost));
-    c->last_err_tile = (h.err_tile == INT_MAX) ? -1 : h.err_tile;
+    c->last_err_tile = (h.err_tile == INT_MAX) ? -1 : h.err_tile + c->err_tile_base;
     c->last_abort = h.abort;
     if (h.abort) return RECON_ETIMEOUT;
     if (c->last_err_tile >= 0) return RECON_EMARKER;
@@ -655,6 +665,23 @@ static cudaError_t copy_rows(void *dst, size_t dpitch, const void *src, size_t s
     return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, st);
 }
 
+// Streams and events of the end-to-end pipeline (created on first use).
+static int ensure_pipeline(recon_ctx *c)
+{
+    if (!c->s_h2d) CK(cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking));
+    if (!c->s_d2h) CK(cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking));
+    for (int s = 0; s < HOST_SEGMENTS; ++s)
+        if (!c->ev_in[s]) CK(cudaEventCreateWithFlags(&c->ev_in[s], cudaEventDisableTiming));
+    return RECON_OK;
+}
+
+// End to end: the batch is cut into up to HOST_SEGMENTS runs of consecutive
+// tiles with about equal pixel counts. All host-to-device copies are queued at
+// once on one stream (an event after each segment); each segment is then
+// reconstructed on the context stream as soon as its inputs have arrived, and
+// its results go back on a third stream while the next segment runs. So the
+// copies overlap the reconstruction instead of adding to it. Every segment's
+// device status is checked before its results are copied back.
 extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
 {
     if (!c || !tiles || n < 1) return RECON_EINVAL;
@@ -673,26 +700,58 @@ extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
     }
     int rc = grow(&c->d_img, &c->cap_img, 2 * total);
     if (rc) return rc;
+    if ((rc = ensure_pipeline(c))) return rc;
+    // the previous call's copies out of d_img are finished (that call waited)
     std::vector<recon_tile> dt(n);
-    for (int t = 0; t < n; ++t) {
-        const recon_tile &T = tiles[t];
-        uint8_t *dI = c->d_img + off[t], *dJ = c->d_img + total + off[t];
-        CK(copy_rows(dI, T.W, T.I, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
-        if (T.op != RECON_OP_FILL_HOLES)   // a FillHoles tile's J is output only
-            CK(copy_rows(dJ, T.W, T.J, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->stream));
-        dt[t] = T;
-        dt[t].I = dI; dt[t].J = dJ; dt[t].pitch = T.W;
+    // segment boundaries: cut when a segment reaches total / HOST_SEGMENTS pixels
+    const int nseg_max = total >= ((size_t)256 << 20) ? HOST_SEGMENTS : 1;
+    std::vector<int> seg_end;
+    {
+        size_t acc = 0;
+        for (int t = 0; t < n; ++t) {
+            acc += (size_t)tiles[t].H * tiles[t].W;
+            const size_t goal = total / (size_t)nseg_max * (seg_end.size() + 1);
+            if (t == n - 1 || ((int)seg_end.size() + 1 < nseg_max && acc >= goal)) seg_end.push_back(t + 1);
+        }
     }
+    const int nseg = (int)seg_end.size();
+    // 1. every input copy, in segment order, on the copy-in stream
+    for (int s = 0, t = 0; s < nseg; ++s) {
+        for (; t < seg_end[s]; ++t) {
+            const recon_tile &T = tiles[t];
+            uint8_t *dI = c->d_img + off[t], *dJ = c->d_img + total + off[t];
+            CK(copy_rows(dI, T.W, T.I, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->s_h2d));
+            if (T.op != RECON_OP_FILL_HOLES)   // a FillHoles tile's J is output only
+                CK(copy_rows(dJ, T.W, T.J, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->s_h2d));
+            dt[t] = T;
+            dt[t].I = dI; dt[t].J = dJ; dt[t].pitch = T.W;
+        }
+        CK(cudaEventRecord(c->ev_in[s], c->s_h2d));
+    }
+    // 2. each segment: reconstruct once its inputs are in, check it, copy it out
     const unsigned fl = c->flags;
-    c->flags &= ~RECON_FLAG_SYNC;
-    rc = batch_impl(c, dt.data(), n, nullptr, nullptr);
-    c->flags = fl;
-    if (rc) { cudaStreamSynchronize(c->stream); return rc; }
-    for (int t = 0; t < n; ++t) {
-        const recon_tile &T = tiles[t];
-        CK(copy_rows(T.J, T.pitch, dt[t].J, T.W, T.W, T.H, cudaMemcpyDeviceToHost, c->stream));
+    c->flags = (fl & ~RECON_FLAG_SYNC) | (nseg > 1 ? RECON_FLAG_NO_GRAPH : 0u);
+    rc = RECON_OK;
+    for (int s = 0, t0 = 0; s < nseg && rc == RECON_OK; t0 = seg_end[s++]) {
+        cudaError_t e = cudaStreamWaitEvent(c->stream, c->ev_in[s], 0);
+        if (e != cudaSuccess) { rc = cuda_status(e); break; }
+        rc = batch_impl(c, dt.data() + t0, seg_end[s] - t0, nullptr, nullptr);
+        c->err_tile_base = t0;                     // failing tiles are reported in the caller's indexing
+        if (rc == RECON_OK) rc = recon_sync(c);   // this segment's device status
+        if (rc != RECON_OK) break;
+        for (int t = t0; t < seg_end[s] && rc == RECON_OK; ++t) {
+            const recon_tile &T = tiles[t];
+            rc = cuda_status(copy_rows(T.J, T.pitch, dt[t].J, T.W, T.W, T.H, cudaMemcpyDeviceToHost, c->s_d2h));
+        }
     }
-    return recon_sync(c);
+    c->flags = fl;
+    const cudaError_t e1 = cudaStreamSynchronize(c->s_h2d), e2 = cudaStreamSynchronize(c->s_d2h);
+    if (rc != RECON_OK) {
+        cudaStreamSynchronize(c->stream);
+        return rc;
+    }
+    if (e1 != cudaSuccess) return cuda_status(e1);
+    return cuda_status(e2);
 }
 
 extern "C" int recon_run_host(recon_ctx *c, const uint8_t *I, uint8_t *J, int H, int W, int conn)
