@@ -818,10 +818,10 @@ __device__ __forceinline__ uint32_t max3u(uint32_t a, uint32_t b, uint32_t c) { 
 // registers: the 3 x 3 centre is read for the propagation test, the outer
 // ring when p has a candidate. Returns the raised neighbours
 // (bit k) with their new values in nv[k]; `own` gets the candidates this
-// thread claimed.
+// thread claimed, and `gm` the groups of BH / 32 block rows it changed.
 template <int BH, int CONN>
 __device__ __forceinline__ unsigned expand(Smem<BH> &S, unsigned *claim, unsigned p, bool act,
-                                           uint32_t (&nv)[CONN], unsigned &own)
+                                           uint32_t (&nv)[CONN], unsigned &own, unsigned &gm)
 {
     constexpr int RB = PW * 4;
     const volatile uint8_t *Jb = (const volatile uint8_t *)S.J;
@@ -905,13 +905,14 @@ __device__ __forceinline__ unsigned expand(Smem<BH> &S, unsigned *claim, unsigne
             raised |= 1u << k;
         }
     }
-    if (raised) {   // rows changed since the block was loaded (0-based rows r - 2, r - 1, r)
+    if (raised) {   // groups of BH / 32 rows changed (0-based rows r - 2, r - 1, r), kept in a register
         const unsigned up = CONN == 8 ? (raised & 0x07u) : (raised & 0x1u);
         const unsigned mid = CONN == 8 ? (raised & 0x18u) : (raised & 0x6u);
         const unsigned dn = CONN == 8 ? (raised & 0xE0u) : (raised & 0x8u);
-        if (up) atomicOr(&S.rowmask[(r - 2) >> 5], 1u << ((r - 2) & 31));
-        if (mid) atomicOr(&S.rowmask[(r - 1) >> 5], 1u << ((r - 1) & 31));
-        if (dn) atomicOr(&S.rowmask[r >> 5], 1u << (r & 31));
+        constexpr int GSH = BH == 32 ? 0 : (BH == 64 ? 1 : (BH == 128 ? 2 : 3));   // log2 rows per group
+        if (up) gm |= 1u << (max(r - 2, 0) >> GSH);
+        if (mid) gm |= 1u << ((r - 1) >> GSH);
+        if (dn) gm |= 1u << (min(r, BH - 1) >> GSH);
     }
     return raised;
 }
@@ -923,7 +924,9 @@ __device__ __forceinline__ unsigned expand(Smem<BH> &S, unsigned *claim, unsigne
 // level L, so one barrier per level suffices. Level L claims pixels in bitmap
 // claim[L % 2]; the other bitmap, last used by level L - 1, is cleared during
 // level L for level L + 1. n0 = size of level 0 (counted in cq[0]; the seeding
-// pass zeroed cq[1], cq[2]). Returns entries processed.
+// pass zeroed cq[1], cq[2]). Returns entries processed; the row groups the
+// levels changed are added to rowmask (whole groups: a write-back of a
+// group's unchanged rows stores the values they already hold).
 constexpr unsigned SOLO_MAX = 32;   // levels this small run in warp 0 alone
 
 template <int BH, int CONN>
@@ -934,6 +937,7 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
     constexpr int NCW = BH * BW / 32;   // claim words per bitmap
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long pops = 0;
+    unsigned gm = 0;   // groups of BH / 32 rows this thread changed
     for (int i = threadIdx.x; i < 2 * NCW; i += NT) (&S.claim[0][0])[i] = 0u;
     __syncthreads();
     unsigned n = n0;
@@ -946,16 +950,19 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
         if (n <= SOLO_MAX) {
             // Thin wavefront: warp 0 runs the levels alone, one pixel per
             // lane, with __syncwarp as the level barrier, while the other
-            // warps wait at one CTA barrier. Claims go to one bitmap and each
-            // owner releases its bits after the level; slots of the next
-            // level come from ballots. When a level outgrows the warp, the
-            // CTA takes it over.
+            // warps wait at one CTA barrier. The levels alternate between the
+            // two claim bitmaps as between the queue buffers; during a level
+            // each lane zeroes the bitmap words that its claims of the level
+            // before set (every set bit has an owner, so whole words can go),
+            // so one __syncwarp per level suffices. Slots of the next level
+            // come from ballots. When a level outgrows the warp, the CTA
+            // takes it over.
             if (warp == 0) {
                 for (int i = lane; i < NCW; i += 32) S.claim[src ^ 1][i] = 0u;
                 __syncwarp();
-                unsigned *claim = S.claim[src];
                 unsigned m = n;
                 int s = src;
+                unsigned pprev = 0, oprev = 0;   // this lane's pixel and owned candidates in the level before
                 while (m > 0 && m <= SOLO_MAX) {
                     if (++L > MAX_LEVELS) {
                         if (lane == 0) set_abort(P, AB_LEVELS);
@@ -964,11 +971,20 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
                     }
                     pops += m;
                     ++nlevels;
+                    if (oprev) {   // zero the bitmap words its claims of the level before set
+                        constexpr int RB = PW * 4;
+                        unsigned *cprev = S.claim[s ^ 1];
+                        const int r = (int)(pprev / (unsigned)RB), x = (int)pprev - r * RB - XOFF;
+                        const int pb = (r - 1) * BW + x;
+#pragma unroll
+                        for (int k = 0; k < CONN; ++k)
+                            if ((oprev >> k) & 1u) cprev[(pb + nb_dy<CONN>(k) * BW + nb_dx<CONN>(k)) >> 5] = 0u;
+                    }
                     const bool act = (unsigned)lane < m;
                     const unsigned p = act ? get_entry(S, gsp, s, lane) : 0u;
                     uint32_t nv[CONN];
                     unsigned own;
-                    const unsigned raised = expand<BH, CONN>(S, claim, p, act, nv, own);
+                    const unsigned raised = expand<BH, CONN>(S, S.claim[s], p, act, nv, own, gm);
                     const unsigned lt = lanemask_lt();
                     unsigned tot = 0;
 #pragma unroll
@@ -978,18 +994,8 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
                         tot += __popc(bk);
                     }
                     __syncwarp();
-                    if (own) {   // release this level's claims
-                        constexpr int RB = PW * 4;
-                        const int r = (int)(p / (unsigned)RB), x = (int)p - r * RB - XOFF;
-                        const int pb = (r - 1) * BW + x;
-#pragma unroll
-                        for (int k = 0; k < CONN; ++k)
-                            if ((own >> k) & 1u) {
-                                const int qb = pb + nb_dy<CONN>(k) * BW + nb_dx<CONN>(k);
-                                atomicAnd(&claim[qb >> 5], ~(1u << (qb & 31)));
-                            }
-                    }
-                    __syncwarp();
+                    pprev = p;
+                    oprev = own;
                     m = tot;
                     s ^= 1;
                 }
@@ -1022,7 +1028,7 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
             const unsigned p = act ? get_entry(S, gsp, src, i) : 0u;
             uint32_t nv[CONN];
             unsigned own;
-            const unsigned raised = expand<BH, CONN>(S, claim, p, act, nv, own);
+            const unsigned raised = expand<BH, CONN>(S, claim, p, act, nv, own, gm);
             if (raised) {
                 unsigned slot = atomicAdd(&S.cq[cnext], (unsigned)__popc(raised));
 #pragma unroll
@@ -1034,6 +1040,11 @@ __device__ unsigned long long run_queue(Smem<BH> &S, const Params &P, uint16_t *
         n = S.cq[cnext];
         src = dst;
         ccur = cnext;
+    }
+    {   // rows of the changed groups, for the write-back
+        constexpr int GS = BH / 32;
+        const unsigned g = __reduce_or_sync(FULL, gm);
+        if ((g >> lane) & 1u) atomicOr(&S.rowmask[(lane * GS) >> 5], ((1u << GS) - 1u) << ((lane * GS) & 31));
     }
     return pops;
 }
