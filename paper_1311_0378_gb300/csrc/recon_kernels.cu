@@ -501,7 +501,9 @@ __device__ __forceinline__ uint32_t compose(uint32_t g, uint32_t f)
 // Row recurrence of the scans. The previous row's result stays in registers
 // (the neighbouring lanes' planes arrive by shuffle, the halo words by a
 // broadcast load), and the next row's mask and marker words are loaded while
-// the current row is computed.
+// the current row is computed. Changed rows and pixels are counted per lane and
+// reduced over the warp once per group of 32 rows, so no row waits on a warp
+// reduction before the next one starts.
 template <int CONN, bool DOWN>
 __device__ __forceinline__ unsigned scan_rows(uint32_t *SJ, const uint32_t *SI, unsigned *rowmask,
                                               unsigned *pairmask, int r0, int r1)
@@ -510,7 +512,7 @@ __device__ __forceinline__ unsigned scan_rows(uint32_t *SJ, const uint32_t *SI, 
     const int step = DOWN ? 1 : -1;
     const int yb = DOWN ? r0 : r1 - 1, ye = DOWN ? r1 : r0 - 1;
     constexpr uint32_t ID_C = 0x00FF00FFu;    // identity map: A = 0, C = 255 (both lanes)
-    unsigned any = 0;
+    unsigned any = 0, rbits = 0;   // this lane's changed pixels; rows it changed in the current group
     __syncwarp();
     const uint32_t pw0 = SJ[(yb - step) * PW + w];
     uint32_t pE = even_plane(pw0), pO = odd_plane(pw0);
@@ -573,21 +575,22 @@ __device__ __forceinline__ unsigned scan_rows(uint32_t *SJ, const uint32_t *SI, 
         const uint32_t dE = rE ^ jE, dO = rO ^ jO;
         const unsigned nd = ((dE & 0xFFFFu) != 0) + ((dE >> 16) != 0) + ((dO & 0xFFFFu) != 0) + ((dO >> 16) != 0);
         if (nd) SJ[y * PW + w] = merge_planes(rE, rO);
-        const unsigned nch = __reduce_add_sync(FULL, nd);
-        if (nch) {
-            any += nch;
-            if (lane == 0) {
-                atomicOr(&rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
-                atomicOr(&pairmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
+        any += nd;
+        rbits |= (nd ? 1u : 0u) << ((y - 1) & 31);
+        if (((DOWN ? y : y - 1) & 31) == 0 || yn == ye) {   // leaving a group of 32 rows (0-based y - 1)
+            const unsigned g = __reduce_or_sync(FULL, rbits);
+            if (lane == 0 && g) {
+                atomicOr(&rowmask[(y - 1) >> 5], g);
+                atomicOr(&pairmask[(y - 1) >> 5], g);
             }
+            rbits = 0;
         }
         pE = rE;
         pO = rO;
         j = jn;
         i = in;
     }
-    __syncwarp();
-    return any;   // pixels changed (warp-uniform)
+    return __reduce_add_sync(FULL, any);   // pixels changed (warp-uniform)
 }
 
 template <int BH, int CONN>
