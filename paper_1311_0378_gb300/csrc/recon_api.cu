@@ -427,7 +427,7 @@ static int stage_meta(recon_ctx *c, const recon_tile *tiles, int n, const int *v
 
 static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *variant, const int *order)
 {
-    if (!c || !tiles || n < 1) return RECON_EINVAL;
+    if (!c || !tiles || n < 1 || n > rk::MAX_TILES) return RECON_EINVAL;
     for (int t = 0; t < n; ++t)
         if (!tile_ok(tiles[t])) return RECON_EINVAL;
     if (variant)

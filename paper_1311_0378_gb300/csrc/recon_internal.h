@@ -19,8 +19,12 @@ constexpr int QCAP = 2048;    // shared-memory queue entries per BFS level
 constexpr int GCAP = 16384;   // global spill entries per BFS level per CTA
 constexpr unsigned EMPTY = 0xFFFFFFFFu;
 
-// block state bits; 0 = queued in the cold list, never visited
+// Block state word: flag bits (no flag = queued in the cold list, never
+// visited) and, above them, the index of the block's tile, written once per
+// launch so that a fetched block's tile comes with the fetch's atomic.
 constexpr unsigned S_RUN = 1u, S_DIRTY = 2u, S_IDLE = 4u, S_VIS = 8u;
+constexpr unsigned S_TILE_SHIFT = 4;   // tile index << S_TILE_SHIFT; at most 2^28 tiles per call
+constexpr int MAX_TILES = 1 << 28;
 
 struct alignas(16) TileDesc {
     const uint8_t *I;
@@ -61,7 +65,7 @@ struct Params {
     const int *order;              // packing order of tiles
     const unsigned *order_base;    // ntiles + 1 cumulative block counts in packing order
     unsigned nblocks;
-    unsigned *state;               // per block
+    unsigned *state;               // per block: S_* flags | tile index << S_TILE_SHIFT
     unsigned long long *ring;      // ring_cap slots: state << 32 | block (see next_item)
     unsigned ring_cap;             // ring slots
     Ctl *ctl;

@@ -151,13 +151,18 @@ __device__ void push_hot(const Params &P, unsigned b)
         const unsigned long long t = atomicAdd(&P.ctl->tail, 1ull);
         unsigned long long *slot = &P.ring[t % P.ring_cap];
         const unsigned lap4 = (unsigned)(t / P.ring_cap) * 4u;
+        // a slot free for this lap holds exactly slot_word(lap4, 0): publish
+        // on that guess first, and otherwise go on from the word the CAS saw
+        unsigned long long w = atomicCAS(slot, slot_word(lap4, 0), slot_word(lap4 + 1, b));
+        if (w == slot_word(lap4, 0)) return;
         bool moved = false;
         for (int it = 0; !moved; ++it) {
-            const unsigned long long w = *(volatile unsigned long long *)slot;
             const unsigned st = (unsigned)(w >> 32);
             if (st == lap4) {                 // free for this lap: publish b
-                if (atomicCAS(slot, w, slot_word(lap4 + 1, b)) == w) return;
-                continue;                     // the ticket holder gave it up meanwhile
+                const unsigned long long prev = atomicCAS(slot, w, slot_word(lap4 + 1, b));
+                if (prev == w) return;
+                w = prev;                     // the ticket holder gave it up meanwhile
+                continue;
             }
             if (st == lap4 + 2) {             // given up: free it for the next lap, move on
                 atomicExch(slot, slot_word(lap4 + 4, 0));
@@ -167,14 +172,18 @@ __device__ void push_hot(const Params &P, unsigned b)
             // an earlier lap's block not yet taken: wait for its consumer
             if (it > (1 << 22)) { set_abort(P, AB_PUSH); return; }
             __nanosleep(64);
+            w = *(volatile unsigned long long *)slot;
         }
     }
 }
 
-// Marks block a as needing (re)processing because a neighbour changed.
-__device__ void notify_block(const Params &P, unsigned a)
+// Marks block a (of the tile whose index is tb >> S_TILE_SHIFT) as needing
+// (re)processing because a neighbour changed. A notified block is idle most of
+// the time, so the first compare-and-swap assumes that state, and later ones
+// start from the word the previous one returned.
+__device__ void notify_block(const Params &P, unsigned a, unsigned tb)
 {
-    unsigned old = *(volatile unsigned *)&P.state[a];
+    unsigned old = tb | S_IDLE | S_VIS;
     unsigned nw;
     for (int it = 0;; ++it) {
         if (it > (1 << 20)) { set_abort(P, AB_NOTIFY); return; }
@@ -1249,17 +1258,18 @@ __device__ bool process_block(Smem<BH> &S, const Params &P, const TileDesc &D, u
             if (bits & (1u << d)) {
                 const int ny = by + dy, nx = bx + dx;
                 if (ny >= 0 && ny < D.nby && nx >= 0 && nx < D.nbx)
-                    notify_block(P, D.block_base + (unsigned)(ny * D.nbx + nx));
+                    notify_block(P, D.block_base + (unsigned)(ny * D.nbx + nx), (unsigned)t << S_TILE_SHIFT);
             }
+        } else if (threadIdx.x == 32) {
+            // meanwhile (another warp): let go of the block unless a neighbour
+            // changed our halo while it ran
+            const unsigned tb = (unsigned)t << S_TILE_SHIFT;
+            const unsigned prev = atomicCAS(&P.state[b], tb | S_RUN | S_VIS, tb | S_IDLE | S_VIS);
+            S.flag = (prev == (tb | S_RUN | S_VIS)) ? 0u : 1u;
+            if (S.flag) atomicAnd(&P.state[b], ~S_DIRTY);
         }
         __syncwarp();
-        if (threadIdx.x == 0) {
-            // let go of the block unless a neighbour changed our halo meanwhile
-            const unsigned prev = atomicCAS(&P.state[b], S_RUN | S_VIS, S_IDLE | S_VIS);
-            S.flag = (prev == (S_RUN | S_VIS)) ? 0u : 1u;
-            if (S.flag) atomicAnd(&P.state[b], ~S_DIRTY);
-            S.notify = 0;
-        }
+        if (threadIdx.x == 0) S.notify = 0;
         save_edges(S);
         for (int i = threadIdx.x; i < BH / 32; i += NT) S.rowmask[i] = 0;
         __syncthreads();
@@ -1329,9 +1339,9 @@ __global__ void __launch_bounds__(NT, BH == 256 ? 2 : (BH == 128 ? 4 : 6)) recon
             const unsigned b = next_item(P);
             S.item = b;
             if (b != EMPTY) {
-                const int t = find_tile(P, b);
-                S.tile = (unsigned)t;
                 const unsigned old = atomicOr(&P.state[b], S_RUN | S_VIS);
+                const int t = (int)(old >> S_TILE_SHIFT);   // written by the init kernel
+                S.tile = (unsigned)t;
                 S.visited = (old & S_VIS) ? 1u : 0u;
                 S.flag = (*(volatile int *)&P.tile_err[t] == 0) ? 1u : 0u;  // one read, shared
             }
@@ -1359,7 +1369,7 @@ __global__ void __launch_bounds__(NT, BH == 256 ? 2 : (BH == 128 ? 4 : 6)) recon
         __syncthreads();
         if (threadIdx.x == 0) {
             // failed tile: drop the block without touching its pixels
-            if (!released) atomicExch(&P.state[b], S_IDLE | S_VIS);
+            if (!released) atomicExch(&P.state[b], ((unsigned)t << S_TILE_SHIFT) | S_IDLE | S_VIS);
             if (t != acc_tile) {
                 flush();
                 acc_tile = t;
@@ -1382,7 +1392,7 @@ __global__ void recon_init_kernel(Params P)
 {
     const size_t n = P.nblocks;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        P.state[i] = 0u;
+        P.state[i] = (unsigned)find_tile(P, (unsigned)i) << S_TILE_SHIFT;   // not queued, not visited
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)P.ring_cap;
          i += (size_t)gridDim.x * blockDim.x)
         P.ring[i] = 0ull;   // state 0: free for lap 0
