@@ -109,6 +109,7 @@ int recon_run_op(recon_ctx *ctx, const uint8_t *I, uint8_t *J, int H, int W, int
  * `tiles` is a HOST array of n descriptors with device image pointers.
  * Tiles must not overlap in memory. With RECON_FLAG_LEARNED the cost model
  * chooses each tile's variant and the packing order (never the pixel values).
+ * 1 <= n <= 2^28 (RECON_EINVAL otherwise).
  * On a device error, recon_last_error_tile names the first failing tile. */
 int recon_batch(recon_ctx *ctx, const recon_tile *tiles, int n);
 
