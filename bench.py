@@ -545,8 +545,9 @@ def phase_rooflines(rc, ctx, stream, Js, J0, desc, tiles, px, flush):
     3 bytes per pixel per directional pass (read I and J, write J; 128-pixel
     block rows counted by the kernel) against the measured HBM copy bandwidth;
     the queue-first variant (no scan pairs) checks |N| neighbours per wavefront
-    entry, each a shared-memory access or compare-and-swap, against the
-    shared-memory atomic-add rate measured here by the micro-benchmark."""
+    entry, each a shared-memory test and, for a candidate, one claim (an
+    atomic OR), against the shared-memory atomic-add rate measured here by the
+    micro-benchmark."""
     import torch
     n = len(desc)
     order = sorted(range(n), key=lambda i: -desc[i][2] * desc[i][3])
@@ -577,7 +578,7 @@ def phase_rooflines(rc, ctx, stream, Js, J0, desc, tiles, px, flush):
             rate = checks / (kms / 1e3)
             res.update({"bound": "shared-memory atomics", "achieved_Gops": round(rate / 1e9, 2),
                         "peak_Gops": round(peak / 1e9, 1), "frac": round(rate / peak, 5),
-                        "unit_op": "one neighbour test / compare-and-swap per neighbour of a popped entry"})
+                        "unit_op": "one neighbour test (and claim, for a candidate) per neighbour of a popped entry"})
         out[name] = res
     return out
 
