@@ -130,13 +130,16 @@ int recon_run_host(recon_ctx *ctx, const uint8_t *I, uint8_t *J, int H, int W, i
 /* End-to-end batch: tiles[].I / tiles[].J are HOST pointers; waits. The J of
  * a FillHoles tile is only written. A batch of 256 Mpx or more is cut into
  * four runs of consecutive tiles with about equal pixel counts, processed as
- * a pipeline: all inputs are copied in on one stream, each run is
- * reconstructed as soon as its inputs have arrived, and its results are
- * copied back while the next run is reconstructed (copies from pinned host
- * memory overlap the reconstruction). Each run's device status is checked
- * before its results are copied back; on an error the call stops there and
- * recon_last_error_tile names the failing tile by its index in `tiles`.
- * recon_get_work and recon_last_kernel_ms then describe the last run. */
+ * a pipeline: a run's inputs are copied in one run ahead of its use, each run
+ * is planned (RECON_FLAG_LEARNED) while the run before it is reconstructed
+ * and then queued behind it, and a run's results are copied back while the
+ * next run is reconstructed (copies from pinned host memory overlap the
+ * reconstruction). Each run's device status is checked before its results are
+ * copied back; on an error no later run's results are copied back, the call
+ * returns once the runs already queued have finished, and
+ * recon_last_error_tile (and recon_sync) report the failing tile by its index
+ * in `tiles`. recon_get_work and recon_last_kernel_ms describe the last run
+ * that was launched. */
 int recon_batch_host(recon_ctx *ctx, const recon_tile *tiles, int n);
 
 /* Waits for the context's stream; returns the device status of the last call. */

@@ -51,14 +51,15 @@ struct recon_ctx {
     cudaEvent_t meta_free = nullptr, ev0 = nullptr, ev1 = nullptr;
     // end-to-end buffers and the copy streams of its pipeline
     uint8_t *d_img = nullptr; size_t cap_img = 0;
-    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
-    cudaEvent_t ev_in[HOST_SEGMENTS] = {};
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_plan = nullptr;
+    cudaEvent_t ev_in[HOST_SEGMENTS] = {}, ev_out[HOST_SEGMENTS] = {};
+    rk::Ctl *h_seg_ctl = nullptr;   // pinned: each segment's control word, copied right after its kernel
     // last call
     int last_n = 0;
     int launched = 0;
     int last_err_tile = -1;
-    int err_tile_base = 0;   // index in the caller's batch of the last launch's first tile
     int last_abort = 0;
+    int host_status = 0;     // 1: last_err_tile / last_abort hold the last recon_batch_host call's status
     // diagnostics: per-warp progress words in mapped host memory
     unsigned *h_trace = nullptr; unsigned *d_trace = nullptr; size_t cap_trace = 0; int trace_on = 0;
     // graph cache
@@ -190,8 +191,12 @@ extern "C" int recon_free(recon_ctx *c)
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (int s = 0; s < HOST_SEGMENTS; ++s)
         if (c->ev_in[s]) cudaEventDestroy(c->ev_in[s]);
+    for (int s = 0; s < HOST_SEGMENTS; ++s)
+        if (c->ev_out[s]) cudaEventDestroy(c->ev_out[s]);
     if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
     if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
+    if (c->s_plan) cudaStreamDestroy(c->s_plan);
+    if (c->h_seg_ctl) cudaFreeHost(c->h_seg_ctl);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     recon_sched_destroy(c->sched);
     delete c;
@@ -540,7 +545,7 @@ static int batch_impl(recon_ctx *c, const recon_tile *tiles, int n, const int *v
 
     c->last_n = n;
     c->last_err_tile = -1;
-    c->err_tile_base = 0;
+    c->host_status = 0;
     const bool use_graph = !(c->flags & RECON_FLAG_NO_GRAPH);
     if (use_graph && c->gexec && sig == c->gsig) {
         // the graph records meta_free itself, right after its descriptor copy
@@ -607,11 +612,13 @@ extern "C" int recon_sync(recon_ctx *c)
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
     if (!c->launched) return RECON_OK;
-    rk::Ctl h;
-    CK(cudaMemcpy(&h, c->d_ctl, sizeof(h), cudaMemcpyDeviceToHost));
-    c->last_err_tile = (h.err_tile == INT_MAX) ? -1 : h.err_tile + c->err_tile_base;
-    c->last_abort = h.abort;
-    if (h.abort) return RECON_ETIMEOUT;
+    if (!c->host_status) {   // a host batch records its own status (its segments share the control word)
+        rk::Ctl h;
+        CK(cudaMemcpy(&h, c->d_ctl, sizeof(h), cudaMemcpyDeviceToHost));
+        c->last_err_tile = (h.err_tile == INT_MAX) ? -1 : h.err_tile;
+        c->last_abort = h.abort;
+    }
+    if (c->last_abort) return RECON_ETIMEOUT;
     if (c->last_err_tile >= 0) return RECON_EMARKER;
     return RECON_OK;
 }
@@ -670,18 +677,24 @@ static int ensure_pipeline(recon_ctx *c)
 {
     if (!c->s_h2d) CK(cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking));
     if (!c->s_d2h) CK(cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking));
-    for (int s = 0; s < HOST_SEGMENTS; ++s)
+    if (!c->s_plan) CK(cudaStreamCreateWithFlags(&c->s_plan, cudaStreamNonBlocking));
+    for (int s = 0; s < HOST_SEGMENTS; ++s) {
         if (!c->ev_in[s]) CK(cudaEventCreateWithFlags(&c->ev_in[s], cudaEventDisableTiming));
+        if (!c->ev_out[s]) CK(cudaEventCreateWithFlags(&c->ev_out[s], cudaEventDisableTiming));
+    }
+    if (!c->h_seg_ctl) CK(cudaMallocHost((void **)&c->h_seg_ctl, sizeof(rk::Ctl) * HOST_SEGMENTS));
     return RECON_OK;
 }
 
 // End to end: the batch is cut into up to HOST_SEGMENTS runs of consecutive
-// tiles with about equal pixel counts. All host-to-device copies are queued at
-// once on one stream (an event after each segment); each segment is then
-// reconstructed on the context stream as soon as its inputs have arrived, and
-// its results go back on a third stream while the next segment runs. So the
-// copies overlap the reconstruction instead of adding to it. Every segment's
-// device status is checked before its results are copied back.
+// tiles with about equal pixel counts. A segment's host-to-device copies are
+// queued on one stream a segment ahead of its use; the segment is planned (the
+// learned schedule's feature pass, on a side stream, once its inputs are in)
+// and launched on the context stream behind the segment before it, so the
+// device runs the segments back to back while the host plans the next one.
+// Each segment's control word is copied to pinned memory right after its
+// kernel; the host checks it when the segment is done and only then queues
+// that segment's results back to the caller on a third stream.
 extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
 {
     if (!c || !tiles || n < 1) return RECON_EINVAL;
@@ -703,6 +716,12 @@ extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
     if ((rc = ensure_pipeline(c))) return rc;
     // the previous call's copies out of d_img are finished (that call waited)
     std::vector<recon_tile> dt(n);
+    for (int t = 0; t < n; ++t) {
+        dt[t] = tiles[t];
+        dt[t].I = c->d_img + off[t];
+        dt[t].J = c->d_img + total + off[t];
+        dt[t].pitch = tiles[t].W;
+    }
     // segment boundaries: cut when a segment reaches total / HOST_SEGMENTS pixels
     const int nseg_max = total >= ((size_t)256 << 20) ? HOST_SEGMENTS : 1;
     std::vector<int> seg_end;
@@ -715,41 +734,67 @@ extern "C" int recon_batch_host(recon_ctx *c, const recon_tile *tiles, int n)
         }
     }
     const int nseg = (int)seg_end.size();
-    // 1. every input copy, in segment order, on the copy-in stream
-    for (int s = 0, t = 0; s < nseg; ++s) {
-        for (; t < seg_end[s]; ++t) {
+    auto first = [&](int s) { return s ? seg_end[s - 1] : 0; };
+    auto queue_inputs = [&](int s) -> int {
+        for (int t = first(s); t < seg_end[s]; ++t) {
             const recon_tile &T = tiles[t];
-            uint8_t *dI = c->d_img + off[t], *dJ = c->d_img + total + off[t];
-            CK(copy_rows(dI, T.W, T.I, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->s_h2d));
+            CK(copy_rows(c->d_img + off[t], T.W, T.I, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->s_h2d));
             if (T.op != RECON_OP_FILL_HOLES)   // a FillHoles tile's J is output only
-                CK(copy_rows(dJ, T.W, T.J, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->s_h2d));
-            dt[t] = T;
-            dt[t].I = dI; dt[t].J = dJ; dt[t].pitch = T.W;
+                CK(copy_rows(dt[t].J, T.W, T.J, T.pitch, T.W, T.H, cudaMemcpyHostToDevice, c->s_h2d));
         }
         CK(cudaEventRecord(c->ev_in[s], c->s_h2d));
-    }
-    // 2. each segment: reconstruct once its inputs are in, check it, copy it out
+        return RECON_OK;
+    };
     const unsigned fl = c->flags;
+    auto launch = [&](int s) -> int {
+        const int t0 = first(s), ns = seg_end[s] - t0;
+        std::vector<int> lv, lo;
+        const int *var = nullptr, *ord = nullptr;
+        if ((fl & RECON_FLAG_LEARNED) && c->sched && recon_sched_has_model(c->sched)) {
+            CK(cudaStreamWaitEvent(c->s_plan, c->ev_in[s], 0));
+            const int prc = recon_sched_plan(c->sched, dt.data() + t0, ns, c->sms, c->s_plan, &lv, &lo);
+            if (prc != RECON_OK) return prc;
+            var = lv.data();
+            ord = lo.data();
+        }
+        CK(cudaStreamWaitEvent(c->stream, c->ev_in[s], 0));
+        const int brc = batch_impl(c, dt.data() + t0, ns, var, ord);
+        if (brc != RECON_OK) return brc;
+        CK(cudaMemcpyAsync(&c->h_seg_ctl[s], c->d_ctl, sizeof(rk::Ctl), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaEventRecord(c->ev_out[s], c->stream));
+        return RECON_OK;
+    };
     c->flags = (fl & ~RECON_FLAG_SYNC) | (nseg > 1 ? RECON_FLAG_NO_GRAPH : 0u);
-    rc = RECON_OK;
-    for (int s = 0, t0 = 0; s < nseg && rc == RECON_OK; t0 = seg_end[s++]) {
-        cudaError_t e = cudaStreamWaitEvent(c->stream, c->ev_in[s], 0);
-        if (e != cudaSuccess) { rc = cuda_status(e); break; }
-        rc = batch_impl(c, dt.data() + t0, seg_end[s] - t0, nullptr, nullptr);
-        c->err_tile_base = t0;                     // failing tiles are reported in the caller's indexing
-        if (rc == RECON_OK) rc = recon_sync(c);   // this segment's device status
+    int err_tile = -1, abort_code = 0;
+    rc = queue_inputs(0);
+    if (rc == RECON_OK && nseg > 1) rc = queue_inputs(1);
+    if (rc == RECON_OK) rc = launch(0);
+    for (int s = 0; s < nseg && rc == RECON_OK; ++s) {
+        if (s + 2 < nseg) rc = queue_inputs(s + 2);
+        if (rc == RECON_OK && s + 1 < nseg) rc = launch(s + 1);   // queued behind segment s
         if (rc != RECON_OK) break;
-        for (int t = t0; t < seg_end[s] && rc == RECON_OK; ++t) {
+        cudaError_t e = cudaEventSynchronize(c->ev_out[s]);
+        if (e != cudaSuccess) { rc = cuda_status(e); break; }
+        const rk::Ctl &h = c->h_seg_ctl[s];
+        if (h.abort || h.err_tile != INT_MAX) {   // this segment failed: its results stay on the device
+            abort_code = h.abort;
+            err_tile = h.err_tile == INT_MAX ? -1 : first(s) + h.err_tile;   // in the caller's indexing
+            rc = h.abort ? RECON_ETIMEOUT : RECON_EMARKER;
+            break;
+        }
+        for (int t = first(s); t < seg_end[s] && rc == RECON_OK; ++t) {
             const recon_tile &T = tiles[t];
             rc = cuda_status(copy_rows(T.J, T.pitch, dt[t].J, T.W, T.W, T.H, cudaMemcpyDeviceToHost, c->s_d2h));
         }
     }
     c->flags = fl;
+    const cudaError_t e0 = cudaStreamSynchronize(c->stream);
     const cudaError_t e1 = cudaStreamSynchronize(c->s_h2d), e2 = cudaStreamSynchronize(c->s_d2h);
-    if (rc != RECON_OK) {
-        cudaStreamSynchronize(c->stream);
-        return rc;
-    }
+    c->last_err_tile = err_tile;
+    c->last_abort = abort_code;
+    c->host_status = 1;
+    if (rc != RECON_OK) return rc;
+    if (e0 != cudaSuccess) return cuda_status(e0);
     if (e1 != cudaSuccess) return cuda_status(e1);
     return cuda_status(e2);
 }

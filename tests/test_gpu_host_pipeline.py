@@ -64,3 +64,53 @@ def test_host_batch_reports_failing_tile_of_a_later_segment():
         assert rc.recon_last_error_tile(ctx) == 17
     finally:
         rc.recon_free(ctx)
+
+
+def test_host_batch_learned_schedule_matches_oracle():
+    """With the learned schedule, each segment is planned on a side stream
+    while the segment before it runs; the results must not change."""
+    from paper_1311_0378_gb300 import cost_model
+    with open(GOLDEN) as f:
+        gold = json.load(f)["workloads"]["batch64"]
+    w = synth.workload("batch64")
+    specs = list(w.tiles[:20])
+    Is, Js = _host_pairs(specs, w.seed)
+    digits = len(gold["tiles"][0]["R"])
+    ctx = rc.recon_init(0, 0, rc.RECON_FLAG_LEARNED)
+    try:
+        cost_model.install(ctx)
+        tiles = [(I.data_ptr(), J.data_ptr(), s.H, s.W, s.W, s.conn) for I, J, s in zip(Is, Js, specs)]
+        rc.check(rc.recon_batch_host(ctx, tiles), "recon_batch_host")
+        bad = [t for t, J in enumerate(Js)
+               if hashlib.sha256(memoryview(J.numpy()).cast("B")).hexdigest()[:digits] != gold["tiles"][t]["R"]]
+        assert not bad, "tiles differing from the oracle: %s" % bad
+    finally:
+        rc.recon_free(ctx)
+
+
+def test_host_batch_failing_first_segment_then_normal_call():
+    """A violation in the first segment is reported while the later segments
+    were already queued behind it; the same context then runs a clean batch."""
+    with open(GOLDEN) as f:
+        gold = json.load(f)["workloads"]["batch64"]
+    w = synth.workload("batch64")
+    specs = list(w.tiles[:20])
+    Is, Js = _host_pairs(specs, w.seed)
+    Is[2][7, 9] = 50     # J > I at one pixel of tile 2 (first segment)
+    Js[2][7, 9] = 60
+    digits = len(gold["tiles"][0]["R"])
+    ctx = rc.recon_init(0, 0, 0)
+    try:
+        tiles = [(I.data_ptr(), J.data_ptr(), s.H, s.W, s.W, s.conn) for I, J, s in zip(Is, Js, specs)]
+        assert rc.recon_batch_host(ctx, tiles) == rc.RECON_EMARKER
+        assert rc.recon_last_error_tile(ctx) == 2
+        assert rc.recon_sync(ctx) == rc.RECON_EMARKER
+        Is, Js = _host_pairs(specs, w.seed)
+        tiles = [(I.data_ptr(), J.data_ptr(), s.H, s.W, s.W, s.conn) for I, J, s in zip(Is, Js, specs)]
+        rc.check(rc.recon_batch_host(ctx, tiles), "recon_batch_host after a failure")
+        assert rc.recon_last_error_tile(ctx) == -1
+        bad = [t for t, J in enumerate(Js)
+               if hashlib.sha256(memoryview(J.numpy()).cast("B")).hexdigest()[:digits] != gold["tiles"][t]["R"]]
+        assert not bad, "tiles differing from the oracle: %s" % bad
+    finally:
+        rc.recon_free(ctx)
