@@ -823,7 +823,7 @@ extern "C" int recon_features(recon_ctx *c, const recon_tile *tiles, int n, floa
     void *d = nullptr, *h = nullptr;
     CK(cudaMalloc(&d, sb));
     cudaError_t e = cudaMallocHost(&h, hb);
-    if (e == cudaSuccess) e = rl_features(rt.data(), n, d, sb, feat, nullptr, 4 * c->sms, c->stream, h, hb);
+    if (e == cudaSuccess) e = rl_features(rt.data(), n, d, sb, feat, nullptr, c->sms, c->stream, h, hb);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d);
     if (h) cudaFreeHost(h);

@@ -40,94 +40,108 @@ __device__ __forceinline__ int find_chunk_tile(const unsigned *chunk_base, int n
 constexpr int NCOUNT = 19;
 constexpr int CHUNK_PX = 1 << 16;   // pixels per chunk of a tile (a whole number of rows, at least one)
 
-// Per-thread counts. The 16 histogram bins are one-hot counters in 8-bit
-// fields of two 64-bit words (bins 0-7 and 8-15: one shift and two adds per
-// pixel), moved into the 32-bit totals at least every 255 pixels; blob pixels,
-// zero markers and J > I violations are plain counters.
-struct Counts {
-    unsigned long long lo = 0, hi = 0;   // 8-bit fields: bins 0..7, 8..15
-    unsigned tot[NCOUNT] = {};
-    unsigned pend = 0;                   // pixels in the 8-bit fields
+constexpr int FT = 256;   // threads of features_kernel
 
-    __device__ __forceinline__ void flush()
-    {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            tot[k] += (unsigned)(lo >> (8 * k)) & 0xFFu;
-            tot[8 + k] += (unsigned)(hi >> (8 * k)) & 0xFFu;
-        }
-        lo = hi = 0;
-        pend = 0;
-    }
-    // one pixel; op: the tile's operation (0 dilation, 1 erosion, 2 FillHoles)
-    __device__ __forceinline__ void add(uint32_t i, uint32_t j, int op)
+// Four pixels at once (bytes of a 32-bit word). d gets the per-byte
+// difference a - b modulo 256 and the high bit of each byte of `borrow` is set
+// where b > a (the bytes subtract independently: the high bit of each byte of
+// a is set first so that no borrow crosses a byte boundary, then restored).
+__device__ __forceinline__ void sub_bytes(uint32_t a, uint32_t b, uint32_t &d, uint32_t &borrow)
+{
+    constexpr uint32_t H = 0x80808080u;
+    d = ((a | H) - (b & ~H)) ^ ((a ^ ~b) & H);
+    borrow = ((~a & b) | (~(a ^ b) & d)) & H;
+}
+
+// Counts of one thread: the 16 histogram bins live in the thread's own column
+// of a shared array (row = bin, column = thread: the 32 lanes of a warp always
+// touch 32 different banks), with row 16 taking the pixels whose I - J bin is
+// undefined (J > I); the blob-pixel, zero-marker and violation counts are
+// registers, counted four pixels at a time.
+struct Counts {
+    unsigned *col;                       // &hist[threadIdx.x], rows FT apart
+    unsigned bright = 0, zero = 0, bad = 0;
+
+    // one 32-bit word of I and of J; op: 0 dilation, 1 erosion, 2 FillHoles
+    __device__ __forceinline__ void add4(uint32_t i, uint32_t j, int op, int npx = 4)
     {
         if (op != 0) {
-            i ^= 0xFFu;
-            j = (op == 2) ? 0u : (j ^ 0xFFu);
+            i = ~i;
+            j = (op == 2) ? 0u : ~j;
         }
-        const bool bad = j > i;
-        const uint32_t bin = (i - j) >> 4;   // 0..15 unless bad
-        const unsigned long long one = bad ? 0ull : (1ull << (8 * (bin & 7)));
-        lo += bin < 8 ? one : 0ull;
-        hi += bin < 8 ? 0ull : one;
-        tot[18] += bad;
-        tot[16] += (i >= 100);
-        tot[17] += (j == 0);
-    }
-    // 16 pixels from one 16-byte vector of I and of J (<= 255 pixels pending)
-    __device__ __forceinline__ void add16(uint4 a, uint4 b, int op)
-    {
-        if (pend > 255 - 16) flush();
-        const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+        uint32_t d, jgt, e, lt100;
+        sub_bytes(i, j, d, jgt);
+        sub_bytes(i, 0x64646464u, e, lt100);   // bytes of I below 100
+        const uint32_t z = ~(((j & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | j | 0x7F7F7F7Fu);   // bytes of J equal to 0
+        const uint32_t valid = npx == 4 ? 0x80808080u : (0x80808080u >> (8 * (4 - npx)));
+        bright += __popc(~lt100 & valid);
+        zero += __popc(z & valid);
+        bad += __popc(jgt & valid);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int s = 0; s < 4; ++s) add((aw[q] >> (8 * s)) & 0xFF, (bw[q] >> (8 * s)) & 0xFF, op);
-        pend += 16;
-    }
-    __device__ __forceinline__ void add1(uint32_t i, uint32_t j, int op)
-    {
-        if (pend > 254) flush();
-        add(i, j, op);
-        pend += 1;
+        for (int b = 0; b < 4; ++b) {
+            if (b >= npx) break;
+            const unsigned bin = ((jgt >> (8 * b + 7)) & 1u) ? 16u : ((d >> (8 * b + 4)) & 15u);
+            col[bin * FT] += 1u;
+        }
     }
 };
 
-__global__ void __launch_bounds__(256) features_kernel(const FeatTile *T, int n, const unsigned *chunk_base,
-                                                       unsigned nchunks, unsigned *counts)
+__global__ void __launch_bounds__(FT) features_kernel(const FeatTile *T, int n, const unsigned *chunk_base,
+                                                      unsigned nchunks, unsigned *counts)
 {
+    __shared__ unsigned hist[17 * FT];
     __shared__ unsigned sh[NCOUNT];
     for (unsigned c = blockIdx.x; c < nchunks; c += gridDim.x) {
         if (threadIdx.x < NCOUNT) sh[threadIdx.x] = 0;
+        for (int b = 0; b < 17; ++b) hist[b * FT + threadIdx.x] = 0u;   // this thread's column
         __syncthreads();
         const int t = find_chunk_tile(chunk_base, n, c);
         const FeatTile d = T[t];
         const int y0 = (int)(c - chunk_base[t]) * d.crow;
         const int rows = min(d.H, y0 + d.crow) - y0;
         Counts loc;
+        loc.col = &hist[threadIdx.x];
         const bool vec = ((d.pitch & 15) == 0) && (((uintptr_t)d.I & 15) == 0) && (((uintptr_t)d.J & 15) == 0);
         // every thread strides over the chunk's 16-byte vectors (rows x W/16),
         // so narrow tiles keep the whole CTA busy and each thread has several
         // loads in flight; the ragged column tail and unaligned tiles go byte by byte
         const int nv = vec ? d.W >> 4 : 0;
         const int nvec = rows * nv;
-#pragma unroll 4
-        for (int e = threadIdx.x; e < nvec; e += blockDim.x) {
-            const int r = e / nv, v = e - r * nv;
+        // (row, vector) of index e, stepped by FT = q rows + rem vectors
+        const int q = nv ? FT / nv : 0, rem = FT - q * nv;
+        int r = nv ? (int)threadIdx.x / nv : 0, v = (int)threadIdx.x - r * nv;
+#pragma unroll 2
+        for (int e = threadIdx.x; e < nvec; e += FT) {
             const size_t o = (size_t)(y0 + r) * d.pitch;
-            loc.add16(__ldg((const uint4 *)(d.I + o) + v), __ldg((const uint4 *)(d.J + o) + v), d.op);
+            const uint4 a = __ldg((const uint4 *)(d.I + o) + v), b = __ldg((const uint4 *)(d.J + o) + v);
+            loc.add4(a.x, b.x, d.op);
+            loc.add4(a.y, b.y, d.op);
+            loc.add4(a.z, b.z, d.op);
+            loc.add4(a.w, b.w, d.op);
+            r += q;
+            v += rem;
+            if (v >= nv) {
+                v -= nv;
+                ++r;
+            }
         }
         const int tw = d.W - 16 * nv;   // pixels per row not covered by vectors
-        for (int e = threadIdx.x; e < rows * tw; e += blockDim.x) {
+        for (int e = threadIdx.x; e < rows * tw; e += FT) {
             const int r = e / tw, x = 16 * nv + (e - r * tw);
             const size_t o = (size_t)(y0 + r) * d.pitch + x;
-            loc.add1(d.I[o], d.J[o], d.op);
+            loc.add4(d.I[o], d.J[o], d.op, 1);
         }
-        loc.flush();
+        if (loc.bright) atomicAdd(&sh[16], loc.bright);
+        if (loc.zero) atomicAdd(&sh[17], loc.zero);
+        if (loc.bad) atomicAdd(&sh[18], loc.bad);
+        __syncthreads();
+        {   // bin (thread & 15) over the 16 columns of thread group (thread >> 4)
+            const int bin = threadIdx.x & 15, g = threadIdx.x >> 4;
+            unsigned s = 0;
 #pragma unroll
-        for (int k = 0; k < NCOUNT; ++k)
-            if (loc.tot[k]) atomicAdd(&sh[k], loc.tot[k]);
+            for (int q = 0; q < FT / 16; ++q) s += hist[bin * FT + g * (FT / 16) + q];
+            if (s) atomicAdd(&sh[bin], s);
+        }
         __syncthreads();
         if (threadIdx.x < NCOUNT && sh[threadIdx.x]) atomicAdd(&counts[t * NCOUNT + threadIdx.x], sh[threadIdx.x]);
         __syncthreads();
@@ -263,8 +277,12 @@ __global__ void adam_kernel(float *theta, float *grad, float *m, float *v, int t
 // host-side launchers (internal)
 
 cudaError_t rl_features(const rl_tile *tiles, int n, void *scratch, size_t scratch_bytes, float *feat_dev,
-                        int *viol_dev, int grid, cudaStream_t st, void *host_stage, size_t stage_bytes)
+                        int *viol_dev, int sms, cudaStream_t st, void *host_stage, size_t stage_bytes)
 {
+    static int occ = 0;   // resident CTAs of features_kernel per SM (it is latency-bound: fill the SMs)
+    if (!occ && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rl::features_kernel, rl::FT, 0) != cudaSuccess)
+        occ = 4;
+    const int grid = std::max(1, occ) * std::max(1, sms);
     // scratch: [FeatTile n][chunk_base n+1][counts n*NCOUNT]
     const size_t o_base = ((sizeof(rl::FeatTile) * n + 15) / 16) * 16;
     const size_t o_cnt = ((o_base + sizeof(unsigned) * (n + 1) + 15) / 16) * 16;
@@ -286,7 +304,7 @@ cudaError_t rl_features(const rl_tile *tiles, int n, void *scratch, size_t scrat
     cudaError_t e = cudaMemcpyAsync(d, h, o_cnt, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d + o_cnt, 0, sizeof(unsigned) * n * rl::NCOUNT, st);
     if (e != cudaSuccess) return e;
-    rl::features_kernel<<<grid, 256, 0, st>>>((const rl::FeatTile *)d, n, (const unsigned *)(d + o_base), acc,
+    rl::features_kernel<<<grid, rl::FT, 0, st>>>((const rl::FeatTile *)d, n, (const unsigned *)(d + o_base), acc,
                                              (unsigned *)(d + o_cnt));
     rl::finalize_kernel<<<(n + 127) / 128, 128, 0, st>>>((const rl::FeatTile *)d, n, (const unsigned *)(d + o_cnt),
                                                          feat_dev, viol_dev);

@@ -16,7 +16,7 @@ struct rl_tile {
 size_t rl_features_scratch(int n);
 size_t rl_features_stage(int n);
 cudaError_t rl_features(const rl_tile *tiles, int n, void *scratch, size_t scratch_bytes, float *feat_dev,
-                        int *viol_dev, int grid, cudaStream_t st, void *host_stage, size_t stage_bytes);
+                        int *viol_dev, int sms, cudaStream_t st, void *host_stage, size_t stage_bytes);
 cudaError_t rl_forward(const float *theta, const float *X, int n, float *Y, cudaStream_t st);
 cudaError_t rl_grad(const float *theta, const float *X, const float *T, const int *idx, int nb, float *grad,
                     float *loss, cudaStream_t st);

@@ -95,7 +95,7 @@ int recon_sched_plan(recon_sched *s, const recon_tile *tiles, int n, int sms, cu
     std::vector<rl_tile> rt(n);
     for (int t = 0; t < n; ++t)
         rt[t] = rl_tile{tiles[t].I, tiles[t].J, tiles[t].H, tiles[t].W, tiles[t].pitch, tiles[t].op};
-    cudaError_t e = rl_features(rt.data(), n, s->d_scratch, s->cap_scratch, s->d_feat, nullptr, 4 * sms, st,
+    cudaError_t e = rl_features(rt.data(), n, s->d_scratch, s->cap_scratch, s->d_feat, nullptr, sms, st,
                                 s->h_stage, s->cap_stage);
     if (e == cudaSuccess) e = rl_forward(s->d_theta, s->d_feat, n, s->d_pred, st);
     s->pred.resize(2 * (size_t)n);

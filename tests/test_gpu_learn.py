@@ -72,6 +72,40 @@ def test_features_match_numpy(ctx):
         np.testing.assert_allclose(got[t, 18:], want[18:], rtol=2e-7)
 
 
+def test_features_of_erosion_fillholes_and_violations(ctx):
+    """Erosion tiles are described by their complemented values, FillHoles tiles
+    by the complemented mask with a zero marker; pixels with J > I take no
+    histogram bin but count in the other features."""
+    specs = [synth.TileSpec(H, W, nb, 3, 20, m, 8, t) for t, (H, W, nb, m) in enumerate([
+        (256, 512, 80, 0), (300, 1024, 40, 1), (128, 256, 30, 0), (129, 257, 30, 1)])]
+    pairs = synth.generate(specs, 22)
+    viol = []
+    for I, J in pairs[2:]:
+        J = J.copy()
+        J[5, :40] = np.minimum(255, I[5, :40].astype(np.int32) + 7).astype(np.uint8)   # J > I on part of a row
+        viol.append((I, J, 0))
+    cases = [(pairs[0][0], 255 - pairs[0][1], 1),          # erosion: J >= I
+             (pairs[1][0], np.zeros_like(pairs[1][1]), 2)]  # FillHoles: J is output only
+    cases += viol                                          # dilation with violations (16-byte and byte paths)
+    devs = [(torch.from_numpy(np.ascontiguousarray(I)).cuda(), torch.from_numpy(np.ascontiguousarray(J)).cuda())
+            for I, J, _ in cases]
+    torch.cuda.synchronize()
+    feat = torch.zeros((len(cases), 20), dtype=torch.float32, device="cuda")
+    tiles = [(a.data_ptr(), b.data_ptr(), I.shape[0], I.shape[1], I.shape[1], 8, op)
+             for (a, b), (I, _, op) in zip(devs, cases)]
+    rc.check(rc.recon_features(ctx, tiles, feat.data_ptr()), "features")
+    got = feat.cpu().numpy()
+    for t, (I, J, op) in enumerate(cases):
+        if op == 1:
+            I, J = 255 - I, 255 - J
+        elif op == 2:
+            I, J = 255 - I, np.zeros_like(J)
+        want = numpy_features(I, J)
+        np.testing.assert_array_equal(got[t, :18], want[:18])
+        np.testing.assert_allclose(got[t, 18:], want[18:], rtol=2e-7)
+    assert all(np.count_nonzero(J.astype(np.int32) > I) > 0 for I, J, _ in viol)
+
+
 def test_forward_matches_oracle(ctx):
     rng = np.random.default_rng(2)
     X = rng.uniform(0, 1, size=(300, 20))
