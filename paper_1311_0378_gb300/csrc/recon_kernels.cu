@@ -735,9 +735,24 @@ __device__ unsigned seed_pass(Smem<BH> &S, uint16_t *gsp, const unsigned *filter
         if (diff) S.J[y * PW + w] = nv;
         if (__any_sync(FULL, diff != 0) && lane == 0)
             atomicOr(&S.rowmask[(y - 1) >> 5], 1u << ((y - 1) & 31));
+        {   // the row's raised pixels join level 0: one slot reservation per warp and row
+            const unsigned lt = lanemask_lt();
+            unsigned off[4], tot = 0;
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-            warp_push(S, gsp, 0, ((diff >> (8 * b)) & 0xFFu) != 0, (uint16_t)((y * PW + w) * 4 + b));
+            for (int b = 0; b < 4; ++b) {
+                const unsigned bk = __ballot_sync(FULL, ((diff >> (8 * b)) & 0xFFu) != 0);
+                off[b] = tot + __popc(bk & lt);
+                tot += __popc(bk);
+            }
+            if (tot) {
+                unsigned base = 0;
+                if (lane == 0) base = atomicAdd(&S.cq[0], tot);
+                base = __shfl_sync(FULL, base, 0);
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if ((diff >> (8 * b)) & 0xFFu) put_entry(S, gsp, 0, base + off[b], (uint16_t)((y * PW + w) * 4 + b));
+            }
+        }
     }
     __syncthreads();
     return S.cq[0];
